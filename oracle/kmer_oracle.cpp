@@ -1,0 +1,221 @@
+/*
+ * CPU oracle for k-mer analysis.  TEST INFRASTRUCTURE ONLY: the tests, the
+ * package smoke check and the benchmark's CPU-baseline leg may call it; the
+ * library never does.  It shares no code with the CUDA path.
+ *
+ * What it computes is the plain definition, written out with strings and an
+ * ordered map (slow on purpose, easy to check by eye):
+ *
+ *  - Sec. II-B (K-mer Analysis using Distributed Histograms): every read is
+ *    split into k-mers that overlap by k-1 bases; each k-mer gets a count, and
+ *    the bases just before and just after it in the read are tallied as its
+ *    left and right extensions.  K-mers seen fewer than min_count times are
+ *    dropped (the paper keeps those "occurring more than epsilon times", so
+ *    min_count = epsilon + 1).
+ *  - A k-mer and its reverse complement are the same de Bruijn vertex
+ *    (Sec. II-C, DNA is double stranded), so each window is stored under the
+ *    smaller (lexicographic, A<C<G<T) of the two strings; when the reverse
+ *    complement is kept, the two extensions swap sides and are complemented.
+ *  - A window containing any byte other than A, C, G, T is skipped.  An
+ *    extension base counts only if it exists in the read, is one of A/C/G/T
+ *    and its Phred quality is at least qual_threshold.
+ *  - Classification of each side (Sec. II-C):
+ *      mode 0, depth adaptive: with m the most common extension and alt the
+ *        sum of the other three tallies, the side is UNIQUE(m) iff
+ *        alt <= t_hq = max(t_base, e * d) where d is the k-mer count and
+ *        e = err_num / err_den (compared exactly in integers); no extension
+ *        at all is DEAD_END; a tie for most common, or too many
+ *        alternatives, is FORK.
+ *      mode 1, static: a base is a high quality extension iff its tally is
+ *        at least t_ext (Sec. II-B); exactly one such base is UNIQUE, none
+ *        is DEAD_END, several are FORK.
+ *    Codes 0..3 = A,C,G,T (unique), 4 = FORK, 5 = DEAD_END.
+ *
+ * Sharded mode (n_shards > 1) keeps only keys whose FNV-1a 64-bit hash of the
+ * key string is congruent to `shard`; it is the same definition restricted to
+ * a subset of keys, so that large inputs fit in host memory.
+ */
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+extern "C" {
+
+typedef struct {
+    uint32_t k;
+    uint32_t min_count;
+    int32_t qual_offset;
+    int32_t qual_threshold;
+    int32_t ext_mode;
+    uint32_t t_base;
+    uint32_t err_num;
+    uint32_t err_den;
+    uint32_t t_ext;
+} oracle_params;
+
+typedef struct {
+    uint64_t n;        /* surviving k-mers */
+    char *keys;        /* n * k characters, ascending */
+    uint64_t *count;   /* n */
+    uint64_t *ext;     /* n * 8: left A,C,G,T then right A,C,G,T */
+    uint8_t *cls;      /* n * 2: left, right */
+    uint64_t windows;  /* valid windows counted (in this shard) */
+    uint64_t distinct; /* distinct canonical k-mers before the count filter */
+} oracle_result;
+
+}  // extern "C"
+
+namespace {
+
+struct Rec {
+    uint64_t count = 0;
+    uint64_t ext[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+};
+
+int base_index(char c) {
+    switch (c) {
+        case 'A': return 0;
+        case 'C': return 1;
+        case 'G': return 2;
+        case 'T': return 3;
+    }
+    return -1;
+}
+
+char complement(char c) {
+    switch (c) {
+        case 'A': return 'T';
+        case 'C': return 'G';
+        case 'G': return 'C';
+        case 'T': return 'A';
+    }
+    return 'N';
+}
+
+std::string reverse_complement(const std::string &s) {
+    std::string r(s.size(), 'N');
+    for (size_t i = 0; i < s.size(); ++i) r[s.size() - 1 - i] = complement(s[i]);
+    return r;
+}
+
+uint64_t fnv1a(const std::string &s) {
+    uint64_t h = 14695981039346656037ull;  // FNV-1a 64 offset basis
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+const uint8_t FORK = 4, DEAD_END = 5;
+
+uint8_t classify(const uint64_t n[4], uint64_t d, const oracle_params &p) {
+    if (p.ext_mode == 1) {
+        int hq = 0, which = 0;
+        for (int b = 0; b < 4; ++b)
+            if (n[b] >= p.t_ext) { ++hq; which = b; }
+        if (hq == 0) return DEAD_END;
+        if (hq == 1) return (uint8_t)which;
+        return FORK;
+    }
+    uint64_t best = 0;
+    int m = 0, ties = 0;
+    for (int b = 0; b < 4; ++b) {
+        if (n[b] > best) { best = n[b]; m = b; ties = 1; }
+        else if (n[b] == best && best > 0) ++ties;
+    }
+    if (best == 0) return DEAD_END;
+    if (ties > 1) return FORK;
+    uint64_t alt = 0;
+    for (int b = 0; b < 4; ++b)
+        if (b != m) alt += n[b];
+    // alt <= max(t_base, (num/den) * d)  <=>  alt*den <= max(t_base*den, num*d)
+    uint64_t lhs = alt * (uint64_t)p.err_den;
+    uint64_t a = (uint64_t)p.t_base * p.err_den, b = (uint64_t)p.err_num * d;
+    return lhs <= (a > b ? a : b) ? (uint8_t)m : FORK;
+}
+
+}  // namespace
+
+extern "C" int oracle_kmer_analysis(const char *bases, const uint8_t *quals, const uint64_t *offsets,
+                                    uint64_t n_reads, const oracle_params *p, uint32_t shard,
+                                    uint32_t n_shards, oracle_result *out) {
+    if (!p || !out || (n_reads && (!bases || !quals || !offsets))) return -1;
+    if (p->k == 0 || n_shards == 0 || shard >= n_shards) return -1;
+    if (p->ext_mode == 0 && p->err_den == 0) return -1;
+    std::memset(out, 0, sizeof(*out));
+    const size_t k = p->k;
+    std::map<std::string, Rec> M;
+    uint64_t windows = 0;
+    for (uint64_t r = 0; r < n_reads; ++r) {
+        const std::string read(bases + offsets[r], bases + offsets[r + 1]);
+        const uint8_t *q = quals + offsets[r];
+        const size_t L = read.size();
+        for (size_t i = 0; i + k <= L; ++i) {
+            std::string w = read.substr(i, k);
+            bool ok = true;
+            for (char c : w)
+                if (base_index(c) < 0) ok = false;
+            if (!ok) continue;
+            std::string u = reverse_complement(w);
+            bool flip = u < w;
+            const std::string &c = flip ? u : w;
+            if (n_shards > 1 && fnv1a(c) % n_shards != shard) continue;
+            ++windows;
+            // candidate extensions in read orientation
+            bool has_l = i > 0, has_r = i + k < L;
+            char lb = has_l ? read[i - 1] : 'N', rb = has_r ? read[i + k] : 'N';
+            int lq = has_l ? (int)q[i - 1] - p->qual_offset : -1;
+            int rq = has_r ? (int)q[i + k] - p->qual_offset : -1;
+            if (flip) {  // the stored key reads the other strand
+                char nl = complement(rb), nr = complement(lb);
+                int nlq = rq, nrq = lq;
+                bool nhl = has_r, nhr = has_l;
+                lb = nl; rb = nr; lq = nlq; rq = nrq; has_l = nhl; has_r = nhr;
+            }
+            Rec &rec = M[c];
+            rec.count += 1;
+            if (has_l && base_index(lb) >= 0 && lq >= p->qual_threshold) rec.ext[0][base_index(lb)] += 1;
+            if (has_r && base_index(rb) >= 0 && rq >= p->qual_threshold) rec.ext[1][base_index(rb)] += 1;
+        }
+    }
+    std::vector<const std::pair<const std::string, Rec> *> keep;
+    for (const auto &kv : M)
+        if (kv.second.count >= p->min_count) keep.push_back(&kv);
+    const uint64_t n = keep.size();
+    out->n = n;
+    out->windows = windows;
+    out->distinct = M.size();
+    out->keys = (char *)std::malloc(n * k + 1);
+    out->count = (uint64_t *)std::malloc(sizeof(uint64_t) * (n + 1));
+    out->ext = (uint64_t *)std::malloc(sizeof(uint64_t) * (8 * n + 1));
+    out->cls = (uint8_t *)std::malloc(2 * n + 1);
+    if (!out->keys || !out->count || !out->ext || !out->cls) return -2;
+    for (uint64_t j = 0; j < n; ++j) {
+        const std::string &key = keep[j]->first;
+        const Rec &rec = keep[j]->second;
+        std::memcpy(out->keys + j * k, key.data(), k);
+        out->count[j] = rec.count;
+        for (int s = 0; s < 2; ++s)
+            for (int b = 0; b < 4; ++b) out->ext[8 * j + 4 * s + b] = rec.ext[s][b];
+        out->cls[2 * j + 0] = classify(rec.ext[0], rec.count, *p);
+        out->cls[2 * j + 1] = classify(rec.ext[1], rec.count, *p);
+    }
+    return 0;
+}
+
+extern "C" void oracle_free(oracle_result *r) {
+    if (!r) return;
+    std::free(r->keys);
+    std::free(r->count);
+    std::free(r->ext);
+    std::free(r->cls);
+    std::memset(r, 0, sizeof(*r));
+}
+
+extern "C" uint64_t oracle_fnv1a(const char *s, uint64_t len) {
+    return fnv1a(std::string(s, s + len));
+}
