@@ -1,0 +1,209 @@
+/*
+ * k-mer analysis on one GB300 GPU (sm_103a) -- C ABI.
+ *
+ * The operation is the first stage of iterative contig generation
+ * (Algorithm 1, K-merAnalysis(k, R)) as defined in Sec. II-B of
+ * "Extreme Scale De Novo Metagenome Assembly" (MetaHipMer): split every read
+ * into k-mers overlapping by k-1 bases, count each k-mer, tally the bases
+ * seen just before and just after it in the reads (its left and right
+ * extensions), drop k-mers seen fewer than min_count times, and classify each
+ * side of every surviving k-mer as a unique extension, a fork or a dead end
+ * (Sec. II-C: contigs follow unique high-quality extensions; the two-letter
+ * code [ACGT][ACGT] names them).
+ *
+ * Definitions used throughout:
+ *  - A base is one of the bytes 'A','C','G','T' (uppercase); any other byte
+ *    is N.  A window (k consecutive bytes of one read) containing an N is
+ *    skipped.  Windows never span two reads.
+ *  - A k-mer and its reverse complement are one vertex: each window is
+ *    counted under the lexicographically smaller of the two (A<C<G<T), its
+ *    "canonical" key.  When the reverse complement is the key, the window's
+ *    left and right neighbours swap sides and are complemented.
+ *  - An extension base counts when it exists in the read, is a base (not N)
+ *    and its Phred quality (byte - qual_offset) is >= qual_threshold.  Every
+ *    window without N is counted regardless of quality.
+ *  - Classes: 0..3 = unique extension A,C,G,T; 4 = FORK; 5 = DEAD_END.
+ *    ext_mode 0 (depth adaptive, Sec. II-C): with m the most common
+ *    extension base and alt the sum of the other three tallies, a side is
+ *    UNIQUE(m) iff alt * err_den <= max(t_base * err_den, err_num * count),
+ *    i.e. alt <= t_hq = max(t_base, e * d) with e = err_num / err_den, exact
+ *    in integers; no extension at all is DEAD_END; a tie for most common is
+ *    FORK.  ext_mode 1 (static, Sec. II-B): bases with tally >= t_ext are
+ *    high-quality extensions; exactly one is UNIQUE, none DEAD_END, more FORK.
+ *
+ * Keys are returned 2 bits per base (A=0, C=1, G=2, T=3), first base most
+ * significant, in W = ceil(2k/64) 64-bit words; word 0 is the most
+ * significant and holds the first 2k - 64(W-1) bits right-aligned.  Numeric
+ * order of (word 0, word 1, ...) equals lexicographic order of the k-mer.
+ *
+ * Error handling: every call returns KMER_OK (0) or a negative KMER_ERR_*
+ * code and never aborts.  Device-side failures (a table or buffer too small,
+ * a bounded wait that gave up) are latched in a device status word and turn
+ * into a retry with larger buffers or into an error code at the next
+ * synchronising call (query).  kmer_last_error_message() describes the last
+ * failure of the calling thread.
+ *
+ * Streams: every handle is bound to one CUDA stream (NULL = the legacy
+ * default stream) and to the device current when it was created.  Calls
+ * marked "asynchronous" only enqueue work on that stream.
+ */
+#ifndef KMER_ANALYSIS_H
+#define KMER_ANALYSIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KMER_OK 0
+#define KMER_ERR_INVALID_ARG (-1)       /* bad pointer, size, k or threshold */
+#define KMER_ERR_OOM (-2)               /* device or host allocation failed */
+#define KMER_ERR_TABLE_FULL (-3)        /* a hash table could not grow enough */
+#define KMER_ERR_COUNTER_OVERFLOW (-4)  /* a count would exceed 2^32 - 1 */
+#define KMER_ERR_TIMEOUT (-5)           /* a bounded device wait gave up */
+#define KMER_ERR_CUDA (-6)              /* a CUDA runtime call failed */
+#define KMER_ERR_BAD_STATE (-7)         /* call out of order (e.g. results before query) */
+#define KMER_ERR_NO_DEVICE (-8)         /* no usable CUDA device */
+
+#define KMER_MAX_K 127
+
+enum kmer_where { KMER_HOST = 0, KMER_DEVICE = 1 };
+enum kmer_ext_mode { KMER_EXT_DEPTH_ADAPTIVE = 0, KMER_EXT_STATIC = 1 };
+enum kmer_class { KMER_CLS_A = 0, KMER_CLS_C = 1, KMER_CLS_G = 2, KMER_CLS_T = 3,
+                  KMER_CLS_FORK = 4, KMER_CLS_DEAD_END = 5 };
+enum kmer_variant {
+    KMER_VARIANT_PARTITIONED = 0, /* hash-partition windows in HBM, count each partition on chip (default) */
+    KMER_VARIANT_HBM_TABLE = 1    /* one open-addressing table in HBM updated by atomics */
+};
+
+typedef struct kmer_readset kmer_readset_t;
+typedef struct kmer_analysis kmer_analysis_t;
+
+/* Parameters of one analysis (Sec. II-B / II-C).  Fill with
+ * kmer_analysis_default_params() and override fields. */
+typedef struct {
+    uint32_t k;              /* odd, 1..127; even k is rejected (a k-mer could be its own reverse complement) */
+    uint32_t min_count;      /* keep k-mers seen >= min_count times (the paper's epsilon + 1); >= 1 */
+    uint32_t qual_offset;    /* byte value of Phred 0 (33 for FASTQ) */
+    uint32_t qual_threshold; /* extension base counts iff Phred >= qual_threshold */
+    uint32_t ext_mode;       /* enum kmer_ext_mode */
+    uint32_t t_base;         /* mode 0: hard floor of t_hq */
+    uint32_t err_num;        /* mode 0: e = err_num / err_den */
+    uint32_t err_den;        /* mode 0: > 0 */
+    uint32_t t_ext;          /* mode 1: tally at which a base is a high-quality extension */
+    uint32_t variant;        /* enum kmer_variant */
+    uint64_t distinct_hint;  /* expected distinct canonical k-mers; 0 = assume every window distinct */
+    uint64_t memory_budget;  /* device bytes the analysis may hold while querying; 0 = 85% of free memory */
+    uint32_t leaf_bits;      /* tuning override: log2 of the number of partitions (0 = automatic) */
+    uint32_t reserved[5];    /* must be zero */
+} kmer_analysis_params;
+
+/* Results of the last query.  Device pointers owned by the analysis; valid
+ * until the next submit, query, reset or destroy of the same handle. */
+typedef struct {
+    uint64_t n;              /* surviving k-mers */
+    uint32_t k;
+    uint32_t words;          /* W = ceil(2k/64) */
+    const uint64_t *keys;    /* n * W words, row-major (key i at keys[i*W]) */
+    const uint32_t *count;   /* n occurrence counts */
+    const uint32_t *ext;     /* n * 8 tallies: left A,C,G,T then right A,C,G,T */
+    const uint8_t *cls;      /* n * 2 classes: left, right (enum kmer_class) */
+    uint64_t windows;        /* windows counted (all valid windows, before the count filter) */
+    uint64_t distinct;       /* distinct canonical k-mers before the count filter */
+} kmer_result_view;
+
+/* Counters of the last query, for tuning and tests. */
+typedef struct {
+    uint64_t windows, distinct, survivors;
+    uint64_t records_emitted;   /* windows written to level-1 partitions, all passes */
+    uint32_t passes;            /* passes over the reads (1 unless memory-bound) */
+    uint32_t pass_bits, l1_bits, l2_bits;
+    uint32_t retries;           /* re-runs after a buffer was too small */
+    uint32_t fallback_leaves;   /* partitions recounted in an HBM table */
+    uint32_t leaf_table_slots;  /* shared-memory table capacity per partition */
+    uint32_t variant;
+    uint64_t device_bytes;      /* device memory held by the analysis */
+    float ms_total;             /* wall time of the query, host clock */
+} kmer_analysis_stats;
+
+/* Fills *p with defaults: min_count 2, qual_offset 33, qual_threshold 20,
+ * depth-adaptive classes with t_base 2, e = 1/10, t_ext 2, partitioned variant. */
+void kmer_analysis_default_params(kmer_analysis_params *p, uint32_t k);
+
+/* Packs reads for the device (step a1).  Reads are given flat: read i is
+ * bases[offsets[i] .. offsets[i+1]) with one quality byte per base in quals
+ * (same indexing); offsets has n_reads + 1 non-decreasing entries, offsets[0]
+ * is normally 0, and every read is shorter than 2^32 bases.  `where` says
+ * whether bases, quals and offsets are host (KMER_HOST, any host memory;
+ * pinned memory copies fastest) or device (KMER_DEVICE) pointers.  The
+ * quality test (Phred >= qual_threshold, Phred = byte - qual_offset) is
+ * applied here, so every analysis that submits this readset must use the
+ * same two values.  The caller keeps ownership of its buffers; they may be
+ * released once this call returns (it synchronises the stream).  The readset
+ * owns its packed copy (about 0.5 byte per base plus 16 bytes per read).
+ * Errors: INVALID_ARG (null pointer with n_reads > 0, decreasing offsets,
+ * a read of 2^32 bases or more), OOM, CUDA. */
+int kmer_readset_create(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
+                        uint32_t qual_offset, uint32_t qual_threshold, int where, void *cuda_stream,
+                        kmer_readset_t **out);
+/* Number of reads and bases of a readset. */
+int kmer_readset_info(const kmer_readset_t *rs, uint64_t *n_reads, uint64_t *n_bases);
+/* Frees a readset.  It must not be submitted to an analysis that has not
+ * yet been queried or reset. */
+int kmer_readset_destroy(kmer_readset_t *rs);
+
+/* Creates an analysis bound to the current device and `cuda_stream`.
+ * Errors: INVALID_ARG (k even, 0 or > 127; min_count 0; err_den 0 in mode 0;
+ * unknown mode or variant; nonzero reserved fields), NO_DEVICE, OOM. */
+int kmer_analysis_create(const kmer_analysis_params *p, void *cuda_stream, kmer_analysis_t **out);
+
+/* Adds a readset to the analysis.  Submits are commutative and may be
+ * repeated (the result counts every submitted read, Sec. II-A use case 1);
+ * the readset must stay alive until the next query or reset.  Cheap: the
+ * counting itself runs in query.  Errors: INVALID_ARG (null, or the readset
+ * was packed with a different qual_offset / qual_threshold). */
+int kmer_analysis_submit(kmer_analysis_t *h, const kmer_readset_t *rs);
+
+/* Packs reads (as kmer_readset_create) into a readset owned by the analysis
+ * and submits it; released at the next reset or destroy. */
+int kmer_analysis_submit_raw(kmer_analysis_t *h, const char *bases, const uint8_t *quals, const uint64_t *offsets,
+                             uint64_t n_reads, int where);
+
+/* Counts, filters and classifies everything submitted since the last reset
+ * (steps a2-a7) and fills *out with device pointers to the survivors, in no
+ * particular order.  Synchronises the stream.  Buffers grow as needed and
+ * are kept for the next query.  Errors: OOM, TABLE_FULL, COUNTER_OVERFLOW,
+ * TIMEOUT, CUDA; the previous results are invalid after an error. */
+int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
+
+/* Copies the survivors of the last query to host memory: keys (n * W words),
+ * count (n), ext (n * 8), cls (n * 2); any pointer may be NULL to skip that
+ * array; `capacity` is the number of k-mers the buffers hold.  Synchronous.
+ * Errors: BAD_STATE (no successful query), INVALID_ARG (capacity < n). */
+int kmer_analysis_copy_results(kmer_analysis_t *h, uint64_t *keys, uint32_t *count, uint32_t *ext, uint8_t *cls,
+                               uint64_t capacity);
+
+/* Counters of the last query. */
+int kmer_analysis_get_stats(const kmer_analysis_t *h, kmer_analysis_stats *out);
+
+/* Forgets submitted readsets and results; keeps device buffers for reuse. */
+int kmer_analysis_reset(kmer_analysis_t *h);
+
+/* Releases the analysis and every buffer it owns.  NULL is accepted. */
+int kmer_analysis_destroy(kmer_analysis_t *h);
+
+/* Static description of an error code. */
+const char *kmer_strerror(int code);
+
+/* Human-readable detail of the last failure on the calling thread. */
+const char *kmer_last_error_message(void);
+
+/* Library version, e.g. "1.0.0". */
+const char *kmer_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KMER_ANALYSIS_H */

@@ -1,0 +1,328 @@
+"""k-mer analysis on one GB300 GPU: Python binding of the C ABI.
+
+Thin ctypes layer over ``libkmer_analysis.so`` (built in-tree by
+``paper_1809_07014_gb300.build``).  The functions carry the C names of
+``include/kmer_analysis.h`` and only marshal arguments; every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if the library is missing or no GPU is present, calls raise.
+
+Convenience wrappers (:class:`ReadSet`, :class:`KmerAnalysis`) accept numpy
+arrays (host) or CUDA torch tensors (device) for the flat read layout
+``bases[offsets[i]:offsets[i+1]]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkmer_analysis.so")
+
+KMER_OK = 0
+KMER_ERR_INVALID_ARG = -1
+KMER_ERR_OOM = -2
+KMER_ERR_TABLE_FULL = -3
+KMER_ERR_COUNTER_OVERFLOW = -4
+KMER_ERR_TIMEOUT = -5
+KMER_ERR_CUDA = -6
+KMER_ERR_BAD_STATE = -7
+KMER_ERR_NO_DEVICE = -8
+KMER_HOST, KMER_DEVICE = 0, 1
+KMER_EXT_DEPTH_ADAPTIVE, KMER_EXT_STATIC = 0, 1
+KMER_VARIANT_PARTITIONED, KMER_VARIANT_HBM_TABLE = 0, 1
+KMER_CLS_FORK, KMER_CLS_DEAD_END = 4, 5
+KMER_MAX_K = 127
+
+
+class KmerError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where} failed: {code} ({detail})")
+        self.code = code
+
+
+class kmer_analysis_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("min_count", ctypes.c_uint32), ("qual_offset", ctypes.c_uint32),
+                ("qual_threshold", ctypes.c_uint32), ("ext_mode", ctypes.c_uint32), ("t_base", ctypes.c_uint32),
+                ("err_num", ctypes.c_uint32), ("err_den", ctypes.c_uint32), ("t_ext", ctypes.c_uint32),
+                ("variant", ctypes.c_uint32), ("distinct_hint", ctypes.c_uint64),
+                ("memory_budget", ctypes.c_uint64), ("leaf_bits", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+class kmer_result_view(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("k", ctypes.c_uint32), ("words", ctypes.c_uint32),
+                ("keys", ctypes.c_void_p), ("count", ctypes.c_void_p), ("ext", ctypes.c_void_p),
+                ("cls", ctypes.c_void_p), ("windows", ctypes.c_uint64), ("distinct", ctypes.c_uint64)]
+
+
+class kmer_analysis_stats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_uint64), ("distinct", ctypes.c_uint64), ("survivors", ctypes.c_uint64),
+                ("records_emitted", ctypes.c_uint64), ("passes", ctypes.c_uint32), ("pass_bits", ctypes.c_uint32),
+                ("l1_bits", ctypes.c_uint32), ("l2_bits", ctypes.c_uint32), ("retries", ctypes.c_uint32),
+                ("fallback_leaves", ctypes.c_uint32), ("leaf_table_slots", ctypes.c_uint32),
+                ("variant", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# exported symbol -> (restype, argtypes)
+_vp, _u32, _u64, _int = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_SIGNATURES = {
+    "kmer_analysis_default_params": (None, [ctypes.POINTER(kmer_analysis_params), _u32]),
+    "kmer_readset_create": (_int, [_vp, _vp, _vp, _u64, _u32, _u32, _int, _vp, ctypes.POINTER(_vp)]),
+    "kmer_readset_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "kmer_readset_destroy": (_int, [_vp]),
+    "kmer_analysis_create": (_int, [ctypes.POINTER(kmer_analysis_params), _vp, ctypes.POINTER(_vp)]),
+    "kmer_analysis_submit": (_int, [_vp, _vp]),
+    "kmer_analysis_submit_raw": (_int, [_vp, _vp, _vp, _vp, _u64, _int]),
+    "kmer_analysis_query": (_int, [_vp, ctypes.POINTER(kmer_result_view)]),
+    "kmer_analysis_copy_results": (_int, [_vp, _vp, _vp, _vp, _vp, _u64]),
+    "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
+    "kmer_analysis_reset": (_int, [_vp]),
+    "kmer_analysis_destroy": (_int, [_vp]),
+    "kmer_strerror": (ctypes.c_char_p, [_int]),
+    "kmer_last_error_message": (ctypes.c_char_p, []),
+    "kmer_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} is missing: build the CUDA library first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != KMER_OK:
+        lib = load_library()
+        raise KmerError(code, where, lib.kmer_last_error_message().decode(errors="replace"))
+
+
+# ------------------------------------------------------------ C-ABI mirrors
+def kmer_analysis_default_params(k: int) -> kmer_analysis_params:
+    p = kmer_analysis_params()
+    load_library().kmer_analysis_default_params(ctypes.byref(p), k)
+    return p
+
+
+def kmer_readset_create(bases: int, quals: int, offsets: int, n_reads: int, qual_offset: int,
+                        qual_threshold: int, where: int, stream: int = 0) -> int:
+    out = _vp()
+    _check(load_library().kmer_readset_create(bases, quals, offsets, n_reads, qual_offset, qual_threshold,
+                                              where, stream or None, ctypes.byref(out)), "kmer_readset_create")
+    return out.value
+
+
+def kmer_readset_info(rs: int) -> tuple[int, int]:
+    n, b = _u64(), _u64()
+    _check(load_library().kmer_readset_info(rs, ctypes.byref(n), ctypes.byref(b)), "kmer_readset_info")
+    return n.value, b.value
+
+
+def kmer_readset_destroy(rs: int) -> None:
+    _check(load_library().kmer_readset_destroy(rs), "kmer_readset_destroy")
+
+
+def kmer_analysis_create(params: kmer_analysis_params, stream: int = 0) -> int:
+    out = _vp()
+    _check(load_library().kmer_analysis_create(ctypes.byref(params), stream or None, ctypes.byref(out)),
+           "kmer_analysis_create")
+    return out.value
+
+
+def kmer_analysis_submit(h: int, rs: int) -> None:
+    _check(load_library().kmer_analysis_submit(h, rs), "kmer_analysis_submit")
+
+
+def kmer_analysis_submit_raw(h: int, bases: int, quals: int, offsets: int, n_reads: int, where: int) -> None:
+    _check(load_library().kmer_analysis_submit_raw(h, bases, quals, offsets, n_reads, where),
+           "kmer_analysis_submit_raw")
+
+
+def kmer_analysis_query(h: int) -> kmer_result_view:
+    v = kmer_result_view()
+    _check(load_library().kmer_analysis_query(h, ctypes.byref(v)), "kmer_analysis_query")
+    return v
+
+
+def kmer_analysis_copy_results(h: int, keys: int, count: int, ext: int, cls: int, capacity: int) -> None:
+    _check(load_library().kmer_analysis_copy_results(h, keys, count, ext, cls, capacity),
+           "kmer_analysis_copy_results")
+
+
+def kmer_analysis_get_stats(h: int) -> kmer_analysis_stats:
+    s = kmer_analysis_stats()
+    _check(load_library().kmer_analysis_get_stats(h, ctypes.byref(s)), "kmer_analysis_get_stats")
+    return s
+
+
+def kmer_analysis_reset(h: int) -> None:
+    _check(load_library().kmer_analysis_reset(h), "kmer_analysis_reset")
+
+
+def kmer_analysis_destroy(h: int) -> None:
+    _check(load_library().kmer_analysis_destroy(h), "kmer_analysis_destroy")
+
+
+def kmer_strerror(code: int) -> str:
+    return load_library().kmer_strerror(code).decode()
+
+
+def kmer_version() -> str:
+    return load_library().kmer_version().decode()
+
+
+# ------------------------------------------------------ convenience layer
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (no copy)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _where(a) -> int:
+    return KMER_DEVICE if (hasattr(a, "is_cuda") and a.is_cuda) else KMER_HOST
+
+
+def _stream_of(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_params(k: int, **kw) -> kmer_analysis_params:
+    p = kmer_analysis_default_params(k)
+    for key, v in kw.items():
+        if not hasattr(p, key):
+            raise AttributeError(f"unknown parameter {key}")
+        setattr(p, key, v)
+    return p
+
+
+class ReadSet:
+    """Packed reads resident on the GPU (step a1)."""
+
+    def __init__(self, bases, quals, offsets, qual_offset: int = 33, qual_threshold: int = 20, stream=None):
+        where = _where(bases)
+        if _where(quals) != where or _where(offsets) != where:
+            raise ValueError("bases, quals and offsets must all be on the host or all on the device")
+        n = len(offsets) - 1
+        if n < 0:
+            raise ValueError("offsets needs n_reads + 1 entries")
+        self.handle = kmer_readset_create(_ptr(bases), _ptr(quals), _ptr(offsets), n, qual_offset,
+                                          qual_threshold, where, _stream_of(stream))
+        self.qual_offset, self.qual_threshold = qual_offset, qual_threshold
+
+    @property
+    def n_reads(self) -> int:
+        return kmer_readset_info(self.handle)[0]
+
+    @property
+    def n_bases(self) -> int:
+        return kmer_readset_info(self.handle)[1]
+
+    def close(self):
+        if self.handle:
+            kmer_readset_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Result:
+    """Survivors copied to the host.  keys: (n, W) uint64 words, word 0 most significant."""
+    k: int
+    keys: np.ndarray
+    count: np.ndarray
+    ext: np.ndarray
+    cls: np.ndarray
+    windows: int
+    distinct: int
+
+    def __len__(self) -> int:
+        return len(self.count)
+
+
+class KmerAnalysis:
+    """One k-mer analysis (create / submit / query / destroy)."""
+
+    def __init__(self, k: int, stream=None, **params):
+        self.params = make_params(k, **params)
+        self.handle = kmer_analysis_create(self.params, _stream_of(stream))
+        self._keep = []
+
+    def submit(self, rs: ReadSet):
+        kmer_analysis_submit(self.handle, rs.handle)
+        self._keep.append(rs)
+
+    def submit_raw(self, bases, quals, offsets):
+        where = _where(bases)
+        kmer_analysis_submit_raw(self.handle, _ptr(bases), _ptr(quals), _ptr(offsets), len(offsets) - 1, where)
+
+    def query(self) -> kmer_result_view:
+        return kmer_analysis_query(self.handle)
+
+    def results(self, view: kmer_result_view | None = None) -> Result:
+        v = view if view is not None else self.query()
+        n, W = int(v.n), int(v.words)
+        keys = np.empty((n, W), dtype=np.uint64)
+        count = np.empty(n, dtype=np.uint32)
+        ext = np.empty((n, 8), dtype=np.uint32)
+        cls = np.empty((n, 2), dtype=np.uint8)
+        kmer_analysis_copy_results(self.handle, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
+        return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def stats(self) -> dict:
+        return kmer_analysis_get_stats(self.handle).as_dict()
+
+    def reset(self):
+        kmer_analysis_reset(self.handle)
+        self._keep.clear()
+
+    def close(self):
+        if self.handle:
+            kmer_analysis_destroy(self.handle)
+            self.handle = 0
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

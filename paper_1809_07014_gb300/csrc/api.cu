@@ -1,0 +1,832 @@
+// Host side of the C ABI declared in include/kmer_analysis.h: readsets,
+// planning (passes, partition bits, buffer sizes), launches, the retry loop
+// that grows any buffer a device kernel found too small, and the HBM-table
+// fallback for partitions that do not fit on chip.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "kmer_analysis.h"
+
+using namespace kmer;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? KMER_ERR_OOM : KMER_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+#define TRY(call)                \
+    do {                         \
+        int rc_ = (call);        \
+        if (rc_ != KMER_OK) return rc_; \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t n) {
+        if (n <= bytes && p) return KMER_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            bytes = 0;
+            cudaGetLastError();
+            return fail(KMER_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return KMER_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct Misc {  // small device counters read back after each pass
+    unsigned long long out_n;
+    unsigned long long stats[4];
+    unsigned int status;
+    unsigned int fb_n;
+};
+
+unsigned long long next_pow2(unsigned long long x) {
+    unsigned long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+unsigned ceil_log2(unsigned long long x) {
+    unsigned b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct kmer_readset {
+    int device = 0;
+    unsigned long long n_reads = 0, n_bases = 0, n_blocks = 0;
+    unsigned qual_offset = 33, qual_threshold = 20;
+    DevBuf blocks, blk_off, offsets;
+    unsigned long long len_stats[kLenHist] = {};
+
+    // Exact number of k-windows (before N filtering) for this k.
+    unsigned long long windows_for(unsigned k) const {
+        unsigned long long w = 0;
+        for (unsigned L = k; L < (unsigned)kLenExact; ++L) w += len_stats[L] * (L - k + 1);
+        const unsigned long long big_n = len_stats[kLenExact], big_sum = len_stats[kLenExact + 1];
+        if (big_n) w += big_sum - (unsigned long long)(k - 1) * big_n;
+        return w;
+    }
+};
+
+struct kmer_analysis {
+    kmer_analysis_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    size_t leaf_smem_budget = 0;
+    std::vector<const kmer_readset*> submitted;
+    std::vector<kmer_readset*> owned;
+    // device buffers
+    DevBuf l1_rec, l1_start, l1_cap, l1_fill;
+    DevBuf l2_rec, l2_base, l2_leafcap, l2_fill, l2_leaf_start, tile_prefix;
+    DevBuf out_keys, out_count, out_ext, out_cls;
+    DevBuf fb_list, hbm, misc;
+    unsigned long long out_cap = 0, fb_cap = 0;
+    Misc* host_misc = nullptr;  // pinned
+    // results
+    bool have_result = false;
+    unsigned long long n_out = 0, res_windows = 0, res_distinct = 0;
+    unsigned long long out_hint = 0;  // survivors of the previous query (buffer sizing)
+    kmer_analysis_stats st{};
+
+    unsigned W() const { return (2 * p.k + 63) / 64; }
+    size_t device_bytes() const {
+        const DevBuf* bs[] = {&l1_rec, &l1_start, &l1_cap, &l1_fill, &l2_rec, &l2_base, &l2_leafcap, &l2_fill,
+                              &l2_leaf_start, &tile_prefix, &out_keys, &out_count, &out_ext, &out_cls,
+                              &fb_list, &hbm, &misc};
+        size_t t = 0;
+        for (auto* b : bs) t += b->bytes;
+        return t;
+    }
+};
+
+namespace {
+
+int validate_params(const kmer_analysis_params* p) {
+    if (!p) return fail(KMER_ERR_INVALID_ARG, "params is NULL");
+    if (p->k == 0 || p->k > KMER_MAX_K || p->k % 2 == 0)
+        return fail(KMER_ERR_INVALID_ARG, "k must be odd and in 1..%d (got %u)", KMER_MAX_K, p->k);
+    if (p->min_count == 0) return fail(KMER_ERR_INVALID_ARG, "min_count must be >= 1");
+    if (p->ext_mode > 1) return fail(KMER_ERR_INVALID_ARG, "unknown ext_mode %u", p->ext_mode);
+    if (p->ext_mode == 0 && p->err_den == 0) return fail(KMER_ERR_INVALID_ARG, "err_den must be > 0");
+    if (p->variant > 1) return fail(KMER_ERR_INVALID_ARG, "unknown variant %u", p->variant);
+    if (p->qual_offset > 255 || p->qual_threshold > 255)
+        return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
+    if (p->leaf_bits > 22) return fail(KMER_ERR_INVALID_ARG, "leaf_bits must be <= 22");
+    for (unsigned r : p->reserved)
+        if (r) return fail(KMER_ERR_INVALID_ARG, "reserved fields must be zero");
+    return KMER_OK;
+}
+
+int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
+                 uint64_t n_reads, int where, cudaStream_t s) {
+    rs->n_reads = n_reads;
+    if (n_reads == 0) return KMER_OK;
+    const char* d_bases = bases;
+    const uint8_t* d_quals = quals;
+    const unsigned long long* d_off = reinterpret_cast<const unsigned long long*>(offsets);
+    DevBuf tmp_bases, tmp_quals;
+    TRY(rs->offsets.ensure((n_reads + 1) * 8));
+    if (where == KMER_HOST) {
+        for (uint64_t i = 0; i < n_reads; ++i) {
+            if (offsets[i + 1] < offsets[i]) return fail(KMER_ERR_INVALID_ARG, "offsets decrease at read %llu", (unsigned long long)i);
+            if (offsets[i + 1] - offsets[i] > 0xFFFFFFFFull)
+                return fail(KMER_ERR_INVALID_ARG, "read %llu is 2^32 bases or longer", (unsigned long long)i);
+        }
+        const unsigned long long nb = offsets[n_reads];
+        TRY(tmp_bases.ensure(nb + 16));
+        TRY(tmp_quals.ensure(nb + 16));
+        CK(cudaMemcpyAsync(tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+        d_bases = tmp_bases.as<char>();
+        d_quals = tmp_quals.as<uint8_t>();
+    } else {
+        CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    d_off = rs->offsets.as<unsigned long long>();
+    // read geometry: blocks per read, length histogram, monotonicity
+    DevBuf nblk, scratch, stats;
+    TRY(nblk.ensure(n_reads * 8));
+    TRY(rs->blk_off.ensure((n_reads + 1) * 8));
+    TRY(scratch.ensure(scan_temp_bytes(n_reads)));
+    const size_t stats_bytes = (kLenHist + 2) * 8;
+    TRY(stats.ensure(stats_bytes));
+    CK(cudaMemsetAsync(stats.p, 0, stats_bytes, s));
+    unsigned int* bad = reinterpret_cast<unsigned int*>(stats.as<unsigned long long>() + kLenHist);
+    CK(launch_read_geometry(d_off, n_reads, nblk.as<unsigned long long>(), stats.as<unsigned long long>(), bad, s));
+    CK(exclusive_scan_u64(nblk.as<unsigned long long>(), rs->blk_off.as<unsigned long long>(), n_reads, scratch.p, s));
+    std::vector<unsigned long long> host(kLenHist + 2);
+    CK(cudaMemcpyAsync(host.data(), stats.p, stats_bytes, cudaMemcpyDeviceToHost, s));
+    unsigned long long total_blocks = 0, first_off = 0, last_off = 0;
+    CK(cudaMemcpyAsync(&total_blocks, rs->blk_off.as<unsigned long long>() + n_reads, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&first_off, d_off, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&last_off, d_off + n_reads, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const unsigned bad_flags = (unsigned)(host[kLenHist] & 0xFFFFFFFFull);
+    if (bad_flags & 1u) return fail(KMER_ERR_INVALID_ARG, "offsets are not non-decreasing");
+    if (bad_flags & 2u) return fail(KMER_ERR_INVALID_ARG, "a read is 2^32 bases or longer");
+    std::memcpy(rs->len_stats, host.data(), sizeof(rs->len_stats));
+    rs->n_blocks = total_blocks;
+    rs->n_bases = last_off - first_off;
+    TRY(rs->blocks.ensure(std::max<unsigned long long>(total_blocks, 1) * sizeof(PackedBlock)));
+    int num_sms = 0;
+    CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, rs->device));
+    CK(launch_pack(d_bases, d_quals, d_off, rs->blk_off.as<unsigned long long>(), n_reads, rs->qual_offset,
+                   rs->qual_threshold, rs->blocks.as<PackedBlock>(), num_sms, s));
+    CK(cudaStreamSynchronize(s));
+    return KMER_OK;
+}
+
+int make_readset(const char* bases, const uint8_t* quals, const uint64_t* offsets, uint64_t n_reads,
+                 uint32_t qual_offset, uint32_t qual_threshold, int where, cudaStream_t s, kmer_readset** out) {
+    if (!out) return fail(KMER_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (n_reads && (!bases || !quals || !offsets))
+        return fail(KMER_ERR_INVALID_ARG, "bases, quals and offsets must be non-NULL when n_reads > 0");
+    if (qual_offset > 255 || qual_threshold > 255)
+        return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KMER_ERR_NO_DEVICE, "no CUDA device");
+    }
+    auto* rs = new (std::nothrow) kmer_readset;
+    if (!rs) return fail(KMER_ERR_OOM, "host allocation failed");
+    rs->device = dev;
+    rs->qual_offset = qual_offset;
+    rs->qual_threshold = qual_threshold;
+    int rc = pack_readset(rs, bases, quals, offsets, n_reads, where, s);
+    if (rc != KMER_OK) {
+        delete rs;
+        return rc;
+    }
+    *out = rs;
+    return KMER_OK;
+}
+
+void destroy_readset(kmer_readset* rs) {
+    rs->blocks.release();
+    rs->blk_off.release();
+    rs->offsets.release();
+    delete rs;
+}
+
+// ------------------------------------------------------------------ planning
+struct Plan {
+    Geometry g;
+    unsigned passes;
+    unsigned long long windows;  // upper bound (N windows included)
+};
+
+Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget, unsigned cap_max) {
+    Plan pl{};
+    Geometry& g = pl.g;
+    g.k = h->p.k;
+    g.W = (2 * g.k + 63) / 64;
+    g.hb = 2 * g.k - 64 * (g.W - 1);
+    g.bt = g.W == 1 ? 2 * g.k : 64;
+    pl.windows = windows;
+    const unsigned long long basis = h->p.distinct_hint ? std::min<unsigned long long>(h->p.distinct_hint, windows)
+                                                        : windows;
+    const unsigned long long target = std::max(64u, cap_max / 2);
+    unsigned p = h->p.leaf_bits ? h->p.leaf_bits : ceil_log2((basis + target - 1) / target);
+    const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
+    p = std::max(p, need);
+    p = std::min(p, g.bt);
+    // passes: records of one pass (two levels, with slack) must fit the budget
+    const double rec_bytes = 8.0 * g.W;
+    unsigned ps = 0;
+    for (;;) {
+        const double win = (double)windows / (double)(1ull << ps);
+        const double bytes = win * rec_bytes * 2.6 + 64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
+        if (bytes <= 0.8 * (double)budget || ps >= p || ps >= 12) break;
+        ++ps;
+    }
+    const unsigned lb = p - ps;
+    unsigned p1, p2;
+    if (lb <= 11) {
+        p1 = lb;
+        p2 = 0;
+    } else {
+        p1 = std::min(11u, (lb + 1) / 2);
+        p2 = lb - p1;
+        if (p2 > 11) { p2 = 11; }
+    }
+    if (ps + p1 < need) p1 = need - ps;
+    g.ps = ps;
+    g.p1 = p1;
+    g.p2 = p2;
+    pl.passes = 1u << ps;
+    return pl;
+}
+
+int read_misc(kmer_analysis* h) {
+    CK(cudaMemcpyAsync(h->host_misc, h->misc.p, sizeof(Misc), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return KMER_OK;
+}
+
+int ensure_output(kmer_analysis* h, unsigned long long cap, unsigned long long keep) {
+    if (cap <= h->out_cap) return KMER_OK;
+    const unsigned W = h->W();
+    cap = std::max(cap, (unsigned long long)1024);
+    DevBuf nk, nc, ne, ncl;
+    TRY(nk.ensure(cap * 8 * W));
+    TRY(nc.ensure(cap * 4));
+    TRY(ne.ensure(cap * 32));
+    TRY(ncl.ensure(cap * 2));
+    if (keep) {
+        CK(cudaMemcpyAsync(nk.p, h->out_keys.p, keep * 8 * W, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(nc.p, h->out_count.p, keep * 4, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(ne.p, h->out_ext.p, keep * 32, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(ncl.p, h->out_cls.p, keep * 2, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    std::swap(h->out_keys, nk);
+    std::swap(h->out_count, nc);
+    std::swap(h->out_ext, ne);
+    std::swap(h->out_cls, ncl);
+    nk.release();
+    nc.release();
+    ne.release();
+    ncl.release();
+    h->out_cap = cap;
+    return KMER_OK;
+}
+
+void fill_job_outputs(kmer_analysis* h, Job& j) {
+    Misc* m = h->misc.as<Misc>();
+    j.out_keys = h->out_keys.as<unsigned long long>();
+    j.out_count = h->out_count.as<unsigned int>();
+    j.out_ext = h->out_ext.as<unsigned int>();
+    j.out_cls = h->out_cls.as<unsigned char>();
+    j.out_cap = h->out_cap;
+    j.out_n = &m->out_n;
+    j.status = &m->status;
+    j.stats = m->stats;
+    j.fb_list = h->fb_list.as<unsigned int>();
+    j.fb_n = &m->fb_n;
+    j.fb_cap = (unsigned)h->fb_cap;
+    j.min_count = h->p.min_count;
+    j.ext_mode = h->p.ext_mode;
+    j.t_base = h->p.t_base;
+    j.err_num = h->p.err_num;
+    j.err_den = h->p.err_den;
+    j.t_ext = h->p.t_ext;
+}
+
+void set_readset(Job& j, const kmer_readset* rs) {
+    j.blocks = rs->blocks.as<PackedBlock>();
+    j.blk_off = rs->blk_off.as<unsigned long long>();
+    j.offsets = rs->offsets.as<unsigned long long>();
+    j.n_reads = rs->n_reads;
+}
+
+// Reset the per-pass device counters; out_n restarts at `out_start`.
+int reset_misc(kmer_analysis* h, unsigned long long out_start) {
+    Misc m{};
+    m.out_n = out_start;
+    std::memcpy(h->host_misc, &m, sizeof m);
+    CK(cudaMemcpyAsync(h->misc.p, h->host_misc, sizeof(Misc), cudaMemcpyHostToDevice, h->stream));
+    return KMER_OK;
+}
+
+int status_error(unsigned st) {
+    if (st & ST_TIMEOUT) return fail(KMER_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & ST_COUNTER_OVERFLOW) return fail(KMER_ERR_COUNTER_OVERFLOW, "a k-mer count exceeded 2^32-1");
+    if (st & ST_TABLE_FULL) return fail(KMER_ERR_TABLE_FULL, "an HBM table ran out of slots");
+    return KMER_OK;
+}
+
+// HBM-table recount of the leaves listed by the leaf kernel.
+int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
+    if (n_fb == 0) return KMER_OK;
+    const unsigned P = 1u << (j.g.p1 + j.g.p2);
+    std::vector<unsigned> leaves(n_fb);
+    CK(cudaMemcpyAsync(leaves.data(), h->fb_list.p, n_fb * 4ull, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<unsigned long long> fill(j.g.p2 ? P : (1u << j.g.p1));
+    CK(cudaMemcpyAsync(fill.data(), j.g.p2 ? h->l2_fill.p : h->l1_fill.p, fill.size() * 8, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long extra_out = 0, max_n = 0;
+    for (unsigned lf : leaves) {
+        extra_out += fill[lf] / h->p.min_count + 1;
+        max_n = std::max(max_n, fill[lf]);
+    }
+    TRY(read_misc(h));
+    const unsigned long long out_now = h->host_misc->out_n;
+    TRY(ensure_output(h, out_now + extra_out, out_now));
+    fill_job_outputs(h, j);
+    const unsigned W = j.g.W;
+    const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * max_n));
+    TRY(h->hbm.ensure(cap * hbm_entry_bytes(W)));
+    for (unsigned lf : leaves) {
+        const unsigned long long c = next_pow2(std::max<unsigned long long>(1024, 2 * fill[lf]));
+        CK(cudaMemsetAsync(h->hbm.p, 0, c * hbm_entry_bytes(W), h->stream));
+        CK(launch_records_insert(j, lf, h->hbm.p, c, h->num_sms, h->stream));
+        CK(launch_hbm_sweep(j, h->hbm.p, c, h->num_sms, h->stream));
+    }
+    TRY(read_misc(h));
+    return status_error(h->host_misc->status);
+}
+
+// One pass of the partitioned variant over every submitted readset.
+int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) {
+    Geometry g = pl.g;
+    const unsigned P1 = 1u << g.p1, P = 1u << (g.p1 + g.p2);
+    const unsigned W = g.W;
+    const unsigned long long pass_windows = (pl.windows + pl.passes - 1) / pl.passes;
+    std::vector<unsigned long long> caps(P1), starts(P1 + 1);
+    {
+        const unsigned long long mean = (pass_windows + P1 - 1) / P1;
+        for (unsigned b = 0; b < P1; ++b) caps[b] = mean + mean / 8 + 1024;
+    }
+    std::vector<unsigned long long> exact_leaf;  // exact level-2 layout after an overflow
+    const unsigned long long out_start = h->n_out;
+    for (unsigned attempt = 0;; ++attempt) {
+        if (attempt > 8) return fail(KMER_ERR_TABLE_FULL, "buffers still too small after %u retries", attempt);
+        starts[0] = 0;
+        for (unsigned b = 0; b < P1; ++b) starts[b + 1] = starts[b] + caps[b];
+        const unsigned long long l1_total = starts[P1];
+        TRY(h->l1_rec.ensure(l1_total * 8 * W + 64));
+        TRY(h->l1_start.ensure((P1 + 1) * 8));
+        TRY(h->l1_cap.ensure(P1 * 8));
+        TRY(h->l1_fill.ensure(P1 * 8));
+        CK(cudaMemcpyAsync(h->l1_start.p, starts.data(), (P1 + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->l1_cap.p, caps.data(), P1 * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemsetAsync(h->l1_fill.p, 0, P1 * 8, h->stream));
+        unsigned long long l2_capacity = 0;
+        if (g.p2) {
+            l2_capacity = exact_leaf.empty() ? l1_total + l1_total / 4 + 66ull * P + 1024 : exact_leaf[P];
+            TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
+            TRY(h->l2_base.ensure(P1 * 8));
+            TRY(h->l2_leafcap.ensure(P1 * 4));
+            TRY(h->l2_fill.ensure(P * 8ull));
+            TRY(h->tile_prefix.ensure((P1 + 1) * 8));
+            if (!exact_leaf.empty()) {
+                TRY(h->l2_leaf_start.ensure((P + 1) * 8ull));
+                CK(cudaMemcpyAsync(h->l2_leaf_start.p, exact_leaf.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice,
+                                   h->stream));
+            }
+        }
+        if (h->fb_cap < 64) {
+            TRY(h->fb_list.ensure(64 * 4));
+            h->fb_cap = 64;
+        }
+        TRY(reset_misc(h, out_start));
+        Job j{};
+        j.g = g;
+        j.pass = pass;
+        j.l1_rec = h->l1_rec.as<unsigned long long>();
+        j.l1_start = h->l1_start.as<unsigned long long>();
+        j.l1_cap = h->l1_cap.as<unsigned long long>();
+        j.l1_fill = h->l1_fill.as<unsigned long long>();
+        if (g.p2) {
+            j.l2_rec = h->l2_rec.as<unsigned long long>();
+            j.l2_base = h->l2_base.as<unsigned long long>();
+            j.l2_leafcap = h->l2_leafcap.as<unsigned int>();
+            j.l2_fill = h->l2_fill.as<unsigned long long>();
+            j.tile_prefix = h->tile_prefix.as<unsigned long long>();
+            j.l2_leaf_start = exact_leaf.empty() ? nullptr : h->l2_leaf_start.as<unsigned long long>();
+        }
+        fill_job_outputs(h, j);
+        for (const kmer_readset* rs : h->submitted) {
+            if (rs->n_reads == 0) continue;
+            set_readset(j, rs);
+            CK(launch_scatter(j, 0, rs->n_reads, h->stream));
+        }
+        // level 2 and leaves may be re-run without re-scattering
+        for (unsigned sub_attempt = 0;; ++sub_attempt) {
+            if (sub_attempt > 8) return fail(KMER_ERR_TABLE_FULL, "leaf buffers still too small after retries");
+            if (g.p2) {
+                CK(cudaMemsetAsync(h->l2_fill.p, 0, P * 8ull, h->stream));
+                // exact leaf layout: the uniform capacities computed by the planner are unused
+                CK(launch_l2_plan(j, exact_leaf.empty() ? l2_capacity : ~0ull, h->stream));
+                CK(launch_repart(j, h->num_sms, h->stream));
+            }
+            CK(launch_leaf(j, cap_max, h->stream));
+            TRY(read_misc(h));
+            const Misc m = *h->host_misc;
+            if (m.status & ST_L1_OVERFLOW) break;  // re-scatter with exact bucket sizes
+            if (m.status & ST_L2_OVERFLOW) {
+                std::vector<unsigned long long> fill(P);
+                CK(cudaMemcpyAsync(fill.data(), h->l2_fill.p, P * 8ull, cudaMemcpyDeviceToHost, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+                exact_leaf.assign(P + 1, 0);
+                for (unsigned i = 0; i < P; ++i) exact_leaf[i + 1] = exact_leaf[i] + fill[i];
+                l2_capacity = exact_leaf[P];
+                TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
+                TRY(h->l2_leaf_start.ensure((P + 1) * 8ull));
+                CK(cudaMemcpyAsync(h->l2_leaf_start.p, exact_leaf.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice,
+                                   h->stream));
+                j.l2_rec = h->l2_rec.as<unsigned long long>();
+                j.l2_leaf_start = h->l2_leaf_start.as<unsigned long long>();
+                h->st.retries++;
+                TRY(reset_misc(h, out_start));
+                continue;
+            }
+            if (m.status & (ST_OUT_OVERFLOW | ST_FALLBACK_FULL)) {
+                if (m.status & ST_OUT_OVERFLOW) TRY(ensure_output(h, m.out_n + m.out_n / 16 + 1024, out_start));
+                if (m.status & ST_FALLBACK_FULL) {
+                    TRY(h->fb_list.ensure((m.fb_n + 64) * 4ull));
+                    h->fb_cap = m.fb_n + 64;
+                }
+                fill_job_outputs(h, j);
+                h->st.retries++;
+                TRY(reset_misc(h, out_start));
+                continue;
+            }
+            TRY(status_error(m.status));
+            h->st.fallback_leaves += m.fb_n;
+            TRY(run_fallbacks(h, j, m.fb_n));
+            const Misc fin = *h->host_misc;
+            if (fin.status & ST_OUT_OVERFLOW) return fail(KMER_ERR_CUDA, "fallback output overflow");
+            h->n_out = fin.out_n;
+            h->res_windows += fin.stats[0];
+            h->res_distinct += fin.stats[1];
+            h->st.records_emitted += fin.stats[2];
+            return KMER_OK;
+        }
+        // level-1 overflow: take the exact bucket demand and re-scatter
+        std::vector<unsigned long long> fill(P1);
+        CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (unsigned b = 0; b < P1; ++b) caps[b] = std::max(caps[b], fill[b]);
+        exact_leaf.clear();
+        h->st.retries++;
+    }
+}
+
+int run_direct(kmer_analysis* h, unsigned long long windows) {
+    const unsigned W = h->W();
+    Geometry g{};
+    g.k = h->p.k;
+    g.W = W;
+    g.hb = 2 * g.k - 64 * (W - 1);
+    g.bt = W == 1 ? 2 * g.k : 64;
+    const unsigned long long basis = h->p.distinct_hint ? h->p.distinct_hint : windows;
+    unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, basis + basis / 3));
+    TRY(ensure_output(h, std::min(windows / h->p.min_count + 1024, basis + 1024), 0));
+    for (unsigned attempt = 0;; ++attempt) {
+        TRY(h->hbm.ensure(cap * hbm_entry_bytes(W)));
+        CK(cudaMemsetAsync(h->hbm.p, 0, cap * hbm_entry_bytes(W), h->stream));
+        TRY(reset_misc(h, 0));
+        Job j{};
+        j.g = g;
+        fill_job_outputs(h, j);
+        for (const kmer_readset* rs : h->submitted) {
+            if (rs->n_reads == 0) continue;
+            set_readset(j, rs);
+            CK(launch_direct_insert(j, h->hbm.p, cap, h->stream));
+        }
+        CK(launch_hbm_sweep(j, h->hbm.p, cap, h->num_sms, h->stream));
+        TRY(read_misc(h));
+        const Misc m = *h->host_misc;
+        if ((m.status & ST_TABLE_FULL) && attempt < 6) {
+            cap *= 2;
+            h->st.retries++;
+            continue;
+        }
+        if (m.status & ST_OUT_OVERFLOW && attempt < 6) {
+            TRY(ensure_output(h, m.out_n + 1024, 0));
+            h->st.retries++;
+            continue;
+        }
+        TRY(status_error(m.status));
+        h->n_out = m.out_n;
+        h->res_windows = m.stats[0];
+        h->res_distinct = m.stats[1];
+        h->st.records_emitted = m.stats[0];
+        return KMER_OK;
+    }
+}
+
+int do_query(kmer_analysis* h) {
+    const auto t0 = std::chrono::steady_clock::now();
+    h->have_result = false;
+    h->n_out = h->res_windows = h->res_distinct = 0;
+    const kmer_analysis_stats zero{};
+    h->st = zero;
+    h->st.variant = h->p.variant;
+    unsigned long long windows = 0;
+    for (const kmer_readset* rs : h->submitted) windows += rs->windows_for(h->p.k);
+    if (windows > 0) {
+        if (h->p.variant == KMER_VARIANT_HBM_TABLE) {
+            TRY(run_direct(h, windows));
+            h->st.passes = 1;
+        } else {
+            const unsigned W = h->W();
+            const unsigned cap_max = leaf_table_cap(W, h->leaf_smem_budget);
+            size_t budget = h->p.memory_budget;
+            if (!budget) {
+                size_t fr = 0, tot = 0;
+                CK(cudaMemGetInfo(&fr, &tot));
+                budget = (size_t)(0.85 * (double)(fr + h->device_bytes()));
+            }
+            const Plan pl = make_plan(h, windows, budget, cap_max);
+            h->st.pass_bits = pl.g.ps;
+            h->st.l1_bits = pl.g.p1;
+            h->st.l2_bits = pl.g.p2;
+            h->st.leaf_table_slots = cap_max;
+            h->st.passes = pl.passes;
+            // output sized from the previous query or a fraction of the windows; grown on demand
+            const unsigned long long bound = windows / h->p.min_count + 1024;
+            unsigned long long want = h->out_hint ? h->out_hint + h->out_hint / 16 + 4096 : windows / 4 + 4096;
+            TRY(ensure_output(h, std::min(bound, want), 0));
+            for (unsigned pass = 0; pass < pl.passes; ++pass) TRY(run_pass(h, pl, pass, cap_max));
+        }
+    }
+    h->out_hint = h->n_out;
+    h->st.windows = h->res_windows;
+    h->st.distinct = h->res_distinct;
+    h->st.survivors = h->n_out;
+    h->st.device_bytes = h->device_bytes();
+    h->st.ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h->have_result = true;
+    return KMER_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void kmer_analysis_default_params(kmer_analysis_params* p, uint32_t k) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->k = k;
+    p->min_count = 2;
+    p->qual_offset = 33;
+    p->qual_threshold = 20;
+    p->ext_mode = KMER_EXT_DEPTH_ADAPTIVE;
+    p->t_base = 2;
+    p->err_num = 1;
+    p->err_den = 10;
+    p->t_ext = 2;
+    p->variant = KMER_VARIANT_PARTITIONED;
+}
+
+int kmer_readset_create(const char* bases, const uint8_t* quals, const uint64_t* offsets, uint64_t n_reads,
+                        uint32_t qual_offset, uint32_t qual_threshold, int where, void* cuda_stream,
+                        kmer_readset_t** out) {
+    return make_readset(bases, quals, offsets, n_reads, qual_offset, qual_threshold, where,
+                        static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+int kmer_readset_info(const kmer_readset_t* rs, uint64_t* n_reads, uint64_t* n_bases) {
+    if (!rs) return fail(KMER_ERR_INVALID_ARG, "readset is NULL");
+    if (n_reads) *n_reads = rs->n_reads;
+    if (n_bases) *n_bases = rs->n_bases;
+    return KMER_OK;
+}
+
+int kmer_readset_destroy(kmer_readset_t* rs) {
+    if (!rs) return KMER_OK;
+    DeviceGuard dg(rs->device);
+    destroy_readset(rs);
+    return KMER_OK;
+}
+
+int kmer_analysis_create(const kmer_analysis_params* p, void* cuda_stream, kmer_analysis_t** out) {
+    if (!out) return fail(KMER_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    TRY(validate_params(p));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KMER_ERR_NO_DEVICE, "no CUDA device");
+    }
+    auto* h = new (std::nothrow) kmer_analysis;
+    if (!h) return fail(KMER_ERR_OOM, "host allocation failed");
+    h->p = *p;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->device = dev;
+    int sms = 0, smem_sm = 0, smem_optin = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(KMER_ERR_NO_DEVICE, "cannot query device %d", dev);
+    }
+    h->num_sms = sms;
+    // two leaf CTAs per SM: half the SM's shared memory minus the per-block reserve and statics
+    h->leaf_smem_budget = std::min<size_t>((size_t)smem_optin, (size_t)smem_sm / 2 - 1024 - 256);
+    if (h->misc.ensure(sizeof(Misc)) != KMER_OK || cudaMallocHost((void**)&h->host_misc, sizeof(Misc)) != cudaSuccess) {
+        cudaGetLastError();
+        h->misc.release();
+        delete h;
+        return fail(KMER_ERR_OOM, "cannot allocate counters");
+    }
+    *out = h;
+    return KMER_OK;
+}
+
+int kmer_analysis_submit(kmer_analysis_t* h, const kmer_readset_t* rs) {
+    if (!h || !rs) return fail(KMER_ERR_INVALID_ARG, "NULL handle or readset");
+    if (rs->qual_offset != h->p.qual_offset || rs->qual_threshold != h->p.qual_threshold)
+        return fail(KMER_ERR_INVALID_ARG, "readset packed with qual_offset/threshold %u/%u, analysis uses %u/%u",
+                    rs->qual_offset, rs->qual_threshold, h->p.qual_offset, h->p.qual_threshold);
+    if (rs->device != h->device) return fail(KMER_ERR_INVALID_ARG, "readset lives on another device");
+    h->submitted.push_back(rs);
+    h->have_result = false;
+    return KMER_OK;
+}
+
+int kmer_analysis_submit_raw(kmer_analysis_t* h, const char* bases, const uint8_t* quals, const uint64_t* offsets,
+                             uint64_t n_reads, int where) {
+    if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    kmer_readset* rs = nullptr;
+    TRY(make_readset(bases, quals, offsets, n_reads, h->p.qual_offset, h->p.qual_threshold, where, h->stream, &rs));
+    h->owned.push_back(rs);
+    h->submitted.push_back(rs);
+    h->have_result = false;
+    return KMER_OK;
+}
+
+int kmer_analysis_query(kmer_analysis_t* h, kmer_result_view* out) {
+    if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
+    DeviceGuard dg(h->device);
+    std::memset(out, 0, sizeof *out);
+    int rc = do_query(h);
+    if (rc != KMER_OK) {
+        h->have_result = false;
+        cudaGetLastError();
+        return rc;
+    }
+    out->n = h->n_out;
+    out->k = h->p.k;
+    out->words = h->W();
+    out->keys = h->out_keys.as<uint64_t>();
+    out->count = h->out_count.as<uint32_t>();
+    out->ext = h->out_ext.as<uint32_t>();
+    out->cls = h->out_cls.as<uint8_t>();
+    out->windows = h->res_windows;
+    out->distinct = h->res_distinct;
+    return KMER_OK;
+}
+
+int kmer_analysis_copy_results(kmer_analysis_t* h, uint64_t* keys, uint32_t* count, uint32_t* ext, uint8_t* cls,
+                               uint64_t capacity) {
+    if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
+    if (!h->have_result) return fail(KMER_ERR_BAD_STATE, "no successful query to copy from");
+    if (capacity < h->n_out) return fail(KMER_ERR_INVALID_ARG, "capacity %llu < %llu results",
+                                         (unsigned long long)capacity, h->n_out);
+    DeviceGuard dg(h->device);
+    const unsigned long long n = h->n_out;
+    if (n) {
+        if (keys) CK(cudaMemcpyAsync(keys, h->out_keys.p, n * 8 * h->W(), cudaMemcpyDeviceToHost, h->stream));
+        if (count) CK(cudaMemcpyAsync(count, h->out_count.p, n * 4, cudaMemcpyDeviceToHost, h->stream));
+        if (ext) CK(cudaMemcpyAsync(ext, h->out_ext.p, n * 32, cudaMemcpyDeviceToHost, h->stream));
+        if (cls) CK(cudaMemcpyAsync(cls, h->out_cls.p, n * 2, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return KMER_OK;
+}
+
+int kmer_analysis_get_stats(const kmer_analysis_t* h, kmer_analysis_stats* out) {
+    if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
+    *out = h->st;
+    return KMER_OK;
+}
+
+int kmer_analysis_reset(kmer_analysis_t* h) {
+    if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    h->submitted.clear();
+    for (kmer_readset* rs : h->owned) destroy_readset(rs);
+    h->owned.clear();
+    h->have_result = false;
+    h->n_out = 0;
+    return KMER_OK;
+}
+
+int kmer_analysis_destroy(kmer_analysis_t* h) {
+    if (!h) return KMER_OK;
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    kmer_analysis_reset(h);
+    DevBuf* bs[] = {&h->l1_rec, &h->l1_start, &h->l1_cap, &h->l1_fill, &h->l2_rec, &h->l2_base, &h->l2_leafcap,
+                    &h->l2_fill, &h->l2_leaf_start, &h->tile_prefix, &h->out_keys, &h->out_count, &h->out_ext,
+                    &h->out_cls, &h->fb_list, &h->hbm, &h->misc};
+    for (auto* b : bs) b->release();
+    if (h->host_misc) cudaFreeHost(h->host_misc);
+    delete h;
+    return KMER_OK;
+}
+
+const char* kmer_strerror(int code) {
+    switch (code) {
+        case KMER_OK: return "ok";
+        case KMER_ERR_INVALID_ARG: return "invalid argument";
+        case KMER_ERR_OOM: return "out of memory";
+        case KMER_ERR_TABLE_FULL: return "hash table full";
+        case KMER_ERR_COUNTER_OVERFLOW: return "counter overflow";
+        case KMER_ERR_TIMEOUT: return "device wait timed out";
+        case KMER_ERR_CUDA: return "CUDA error";
+        case KMER_ERR_BAD_STATE: return "call out of order";
+        case KMER_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown error";
+}
+
+const char* kmer_last_error_message(void) { return g_err.c_str(); }
+
+const char* kmer_version(void) { return "1.0.0"; }
+
+}  // extern "C"

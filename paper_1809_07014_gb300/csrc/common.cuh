@@ -1,0 +1,205 @@
+// Shared device definitions of the k-mer analysis library (sm_103a).
+//
+// Data layout in HBM
+//   PackedBlock  : 32 bases of one read, 2 bits per base MSB-first
+//                  (A=0, C=1, G=2, T=3, so numeric order = lexicographic
+//                  order), plus an N bit and a high-quality bit per base.
+//                  Every read starts on a block boundary.
+//   key          : a canonical k-mer as W = ceil(2k/64) 64-bit words, word 0
+//                  most significant (it holds the first 2k - 64(W-1) bits).
+//   record       : one k-mer window after partitioning: W words.  Words
+//                  0..W-2 are the key's head words verbatim; word W-1 (the
+//                  "tail") holds the low bits of z, a bijective mix of the
+//                  key's last word, with the partition bits of z removed
+//                  (they are implied by the partition the record sits in),
+//                  shifted left by 6, and the window's extension code e5 in
+//                  the low 5 bits.
+//
+// The partitioning is the device-wide form of the paper's owner-computes
+// k-mer histogram (Sec. II-A, use case 4; Sec. II-B): a hash of the k-mer
+// picks its owner (a pass, a level-1 bucket, a leaf), and each leaf is then
+// counted alone in an on-chip table.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kmer {
+
+constexpr int kMaxW = 4;
+constexpr int kMaxK = 127;
+
+struct __align__(16) PackedBlock {
+    unsigned long long bases;  // base j at bits [63-2j-1, 63-2j] (MSB first)
+    unsigned int nmask;        // bit j = base j is not A/C/G/T
+    unsigned int hqmask;       // bit j = Phred(base j) >= quality threshold
+};
+
+// Device status word bits (latched; the host reads them after a query).
+enum StatusBits : unsigned int {
+    ST_L1_OVERFLOW = 1u << 0,    // a level-1 bucket got more records than its capacity
+    ST_L2_OVERFLOW = 1u << 1,    // a leaf got more records than its capacity
+    ST_OUT_OVERFLOW = 1u << 2,   // more survivors than the output capacity
+    ST_FALLBACK_FULL = 1u << 3,  // more overflowing leaves than the fallback list holds
+    ST_TABLE_FULL = 1u << 4,     // an HBM table ran out of slots
+    ST_TIMEOUT = 1u << 5,        // a bounded spin gave up
+    ST_COUNTER_OVERFLOW = 1u << 6,
+};
+
+// Extension code of one window: left and right in {0 = none, 1..4 = A,C,G,T + 1}.
+__host__ __device__ inline unsigned ext_code(unsigned left, unsigned right) { return left * 5u + right; }
+
+// Record tail bit that marks an occupied table key (e5 < 25 never sets it).
+constexpr unsigned long long kKeyMark = 32ull;
+constexpr unsigned long long kBusy = 1ull;
+
+// ---------------------------------------------------------------- mixing
+__host__ __device__ constexpr unsigned long long inv_odd(unsigned long long c) {
+    unsigned long long x = c;  // Newton iteration for the inverse mod 2^64
+    for (int i = 0; i < 6; ++i) x *= 2ull - c * x;
+    return x;
+}
+constexpr unsigned long long kM1 = 0xBF58476D1CE4E5B9ull;
+constexpr unsigned long long kM2 = 0x94D049BB133111EBull;
+constexpr unsigned long long kM1i = inv_odd(kM1);
+constexpr unsigned long long kM2i = inv_odd(kM2);
+static_assert(kM1 * kM1i == 1ull && kM2 * kM2i == 1ull, "odd inverses");
+
+__host__ __device__ inline unsigned long long low_mask(unsigned b) {
+    return b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+}
+
+// Inverse of x ^= x >> s on b-bit values.
+__host__ __device__ inline unsigned long long unxorshift(unsigned long long y, unsigned s) {
+    unsigned long long x = y;
+    for (unsigned t = s; t < 64; t += s) x ^= y >> t;
+    return x;
+}
+
+// A bijection on b-bit integers (2 <= b <= 64): xorshift-multiply rounds,
+// each invertible on b bits (splitmix64 finalizer shape, constants shared).
+__host__ __device__ inline unsigned long long mix_bits(unsigned long long x, unsigned b) {
+    const unsigned long long m = low_mask(b);
+    const unsigned s = b > 2 ? (b + 1) / 2 : 1;
+    x ^= x >> s;
+    x = (x * kM1) & m;
+    x ^= x >> s;
+    x = (x * kM2) & m;
+    x ^= x >> s;
+    return x;
+}
+__host__ __device__ inline unsigned long long unmix_bits(unsigned long long z, unsigned b) {
+    const unsigned long long m = low_mask(b);
+    const unsigned s = b > 2 ? (b + 1) / 2 : 1;
+    z = unxorshift(z, s) & m;
+    z = (z * kM2i) & m;
+    z = unxorshift(z, s) & m;
+    z = (z * kM1i) & m;
+    z = unxorshift(z, s) & m;
+    return z;
+}
+
+// Hash of the head words (words 0..W-2) that is xored into the tail before
+// mixing, so that z depends on the whole key.
+template <int W>
+__host__ __device__ inline unsigned long long head_hash(const unsigned long long (&w)[W]) {
+    unsigned long long h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i) h = mix_bits(h ^ w[i], 64);
+    return W > 1 ? h : 0ull;
+}
+
+// Geometry of one analysis: k-mer words, mixing width and partition bits.
+struct Geometry {
+    unsigned k, W;
+    unsigned hb;   // bits in key word 0
+    unsigned bt;   // bits of z (2k for W == 1, else 64)
+    unsigned ps;   // pass bits (top of z)
+    unsigned p1;   // level-1 bucket bits
+    unsigned p2;   // level-2 (leaf within bucket) bits
+    __host__ __device__ unsigned zl_bits() const { return bt - ps - p1; }  // bits of z kept in the record
+};
+
+template <int W>
+__host__ __device__ inline unsigned long long key_to_z(const unsigned long long (&key)[W], unsigned bt) {
+    return W == 1 ? mix_bits(key[0], bt) : mix_bits(key[W - 1] ^ head_hash<W>(key), 64);
+}
+// Recover the key's last word from z and the head words.
+template <int W>
+__host__ __device__ inline unsigned long long z_to_tail(unsigned long long z, const unsigned long long (&key)[W],
+                                                     unsigned bt) {
+    return W == 1 ? unmix_bits(z, bt) : (unmix_bits(z, 64) ^ head_hash<W>(key));
+}
+
+// ------------------------------------------------------- job description
+// Everything one k-mer analysis needs on the device, for one pass.
+struct Job {
+    // packed reads
+    const PackedBlock* blocks;
+    const unsigned long long* blk_off;  // n_reads + 1 block offsets
+    const unsigned long long* offsets;  // n_reads + 1 base offsets
+    unsigned long long n_reads;
+    Geometry g;
+    unsigned pass;
+    // level-1 buckets (P1 = 1 << g.p1)
+    unsigned long long* l1_rec;            // records, W words each
+    const unsigned long long* l1_start;    // record index of each bucket
+    const unsigned long long* l1_cap;      // capacity (records) of each bucket
+    unsigned long long* l1_fill;           // records offered to each bucket
+    // level-2 leaves (P = 1 << (p1 + p2)); unused when p2 == 0
+    unsigned long long* l2_rec;
+    unsigned long long* l2_base;           // per bucket: record index of its first leaf
+    unsigned int* l2_leafcap;              // per bucket: capacity of each of its leaves
+    unsigned long long* l2_fill;           // per leaf: records offered
+    const unsigned long long* l2_leaf_start;  // per leaf + 1: exact layout (after an overflow) or null
+    unsigned long long* tile_prefix;       // per bucket + 1: level-2 tiles before it
+    // outputs (survivors)
+    unsigned long long* out_keys;  // n * W
+    unsigned int* out_count;
+    unsigned int* out_ext;         // n * 8
+    unsigned char* out_cls;        // n * 2
+    unsigned long long out_cap;
+    unsigned long long* out_n;     // survivors written (atomic)
+    // overflow leaves handed to the HBM-table fallback
+    unsigned int* fb_list;
+    unsigned int* fb_n;
+    unsigned int fb_cap;
+    // classification
+    unsigned min_count, ext_mode, t_base, err_num, err_den, t_ext;
+    // status and statistics
+    unsigned int* status;
+    unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted
+};
+
+// ------------------------------------------------------------ classify
+// One side of a k-mer: tallies n[4], count d.  Codes 0..3 = unique base,
+// 4 = fork, 5 = dead end.  Mode 0 is the depth-adaptive rule of Sec. II-C
+// (extend iff at most t_hq = max(t_base, e*d) extensions contradict the most
+// common one, e = err_num/err_den, compared exactly); mode 1 the static
+// high-quality-extension count t_ext of Sec. II-B.
+__device__ inline unsigned char classify_side(const unsigned (&n)[4], unsigned d, const Job& j) {
+    if (j.ext_mode == 1) {
+        int hq = 0, which = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (n[b] >= j.t_ext) { ++hq; which = b; }
+        return hq == 0 ? 5 : (hq == 1 ? (unsigned char)which : 4);
+    }
+    unsigned best = 0, total = 0;
+    int m = 0, ties = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        total += n[b];
+        if (n[b] > best) { best = n[b]; m = b; ties = 1; }
+        else if (n[b] == best) ++ties;
+    }
+    if (best == 0) return 5;
+    if (ties > 1) return 4;
+    unsigned long long alt = (unsigned long long)(total - best) * j.err_den;
+    unsigned long long a = (unsigned long long)j.t_base * j.err_den;
+    unsigned long long e = (unsigned long long)j.err_num * d;
+    return alt <= (a > e ? a : e) ? (unsigned char)m : 4;
+}
+
+__device__ inline void set_status(const Job& j, unsigned bits) { atomicOr(j.status, bits); }
+
+}  // namespace kmer

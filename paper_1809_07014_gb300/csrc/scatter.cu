@@ -1,0 +1,113 @@
+// Level-1 scatter: one thread per read rolls its k-windows (a2, a3), turns
+// each into a W-word record and hands it to the level-1 bucket picked by the
+// top bits of the mixed key.  This is the all-to-all k-mer exchange of the
+// paper's k-mer analysis (Sec. II-B), done as a device-wide partition in HBM:
+// a bucket plays the role of the owning processor.
+#include "kernels.h"
+#include "roll.cuh"
+#include "stage.cuh"
+
+namespace kmer {
+
+template <int W>
+struct ScatterShape {
+    static constexpr unsigned R = W == 1 ? 16 : (W == 2 ? 8 : 4);  // read positions per round
+    static constexpr unsigned S = R * kStageThreads;                 // staged records per round
+};
+
+struct L1Dest {
+    unsigned long long* fill;
+    const unsigned long long* startp;
+    const unsigned long long* capp;
+    __device__ unsigned long long reserve(unsigned d, unsigned n) { return atomicAdd(fill + d, (unsigned long long)n); }
+    __device__ unsigned long long start(unsigned d) const { return __ldg(startp + d); }
+    __device__ unsigned long long cap(unsigned d) const { return __ldg(capp + d); }
+};
+
+template <int W>
+__global__ void __launch_bounds__(kStageThreads, 2)
+scatter_kernel(const Job j, const unsigned long long r0, const unsigned long long r1) {
+    constexpr unsigned R = ScatterShape<W>::R, S = ScatterShape<W>::S;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_maxlen;
+    const unsigned P = 1u << j.g.p1;
+    StageBufs b = carve_stage(smem, W, S, P);
+    if (threadIdx.x == 0) s_maxlen = 0;
+    for (unsigned d = threadIdx.x; d < P; d += kStageThreads) b.hist[d] = 0;
+    __syncthreads();
+
+    const unsigned long long r = r0 + (unsigned long long)blockIdx.x * kStageThreads + threadIdx.x;
+    Roll<W> roll;
+    unsigned long long L = 0;
+    const bool have = r < r1;
+    if (have) {
+        roll.init(j, r);
+        L = roll.L;
+        atomicMax(&s_maxlen, (unsigned)L);
+    }
+    __syncthreads();
+    const unsigned long long steps = (unsigned long long)s_maxlen + 1;
+    const unsigned long long rounds = (steps + R - 1) / R;
+    L1Dest dest{j.l1_fill, j.l1_start, j.l1_cap};
+    unsigned emitted = 0;
+    for (unsigned long long round = 0; round < rounds; ++round) {
+#pragma unroll 1
+        for (unsigned s = 0; s < R; ++s) {
+            const unsigned long long t = round * R + s;
+            const unsigned e = s * kStageThreads + threadIdx.x;
+            unsigned m = 0xFFFFFFFFu;
+            if (have && t <= L) {
+                unsigned long long key[W], rec[W];
+                unsigned lc = 0, rc = 0, bucket = 0;
+                if (roll.step(t, key, lc, rc) && make_record<W>(j.g, j.pass, key, lc, rc, rec, bucket)) {
+                    const unsigned rank = atomicAdd(&b.hist[bucket], 1u);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[w];
+                    m = (bucket << 16) | rank;
+                    ++emitted;
+                }
+            }
+            b.meta[e] = m;
+        }
+        flush_stage<W>(b, S, P, dest, j.l1_rec, j.status, ST_L1_OVERFLOW);
+    }
+    // windows emitted into this pass (a check against the leaves' totals)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) emitted += __shfl_xor_sync(0xffffffffu, emitted, o);
+    if ((threadIdx.x & 31) == 0 && emitted) atomicAdd(j.stats + 2, (unsigned long long)emitted);
+}
+
+size_t scatter_smem_bytes(unsigned W, unsigned p1) {
+    const unsigned P = 1u << p1;
+    switch (W) {
+        case 1: return stage_smem_bytes(1, ScatterShape<1>::S, P);
+        case 2: return stage_smem_bytes(2, ScatterShape<2>::S, P);
+        case 3: return stage_smem_bytes(3, ScatterShape<3>::S, P);
+        default: return stage_smem_bytes(4, ScatterShape<4>::S, P);
+    }
+}
+
+template <int W>
+static cudaError_t launch_scatter_w(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
+    const size_t smem = scatter_smem_bytes(W, j.g.p1);
+    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned long long n = r1 - r0;
+    const unsigned long long grid = (n + kStageThreads - 1) / kStageThreads;
+    if (grid == 0) return cudaSuccess;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    scatter_kernel<W><<<(unsigned)grid, kStageThreads, smem, s>>>(j, r0, r1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
+    switch (j.g.W) {
+        case 1: return launch_scatter_w<1>(j, r0, r1, s);
+        case 2: return launch_scatter_w<2>(j, r0, r1, s);
+        case 3: return launch_scatter_w<3>(j, r0, r1, s);
+        case 4: return launch_scatter_w<4>(j, r0, r1, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace kmer

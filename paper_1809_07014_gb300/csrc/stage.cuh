@@ -1,0 +1,153 @@
+// Shared-memory staging of partitioned records: records of one round are
+// counted per destination in shared memory, one global atomic per
+// destination reserves their slots, and the records are written out sorted
+// by destination so that each warp stores contiguous runs.  This is the
+// aggregation of fine-grained inserts into batch updates that the paper
+// describes for update-only hash-table phases (Sec. II-A, use case 1).
+#pragma once
+#include "common.cuh"
+
+namespace kmer {
+
+constexpr int kStageThreads = 256;
+
+// Exclusive scan across the 256 threads of the block (all must call).
+__device__ inline unsigned block_scan_u32(unsigned v, unsigned* warp_tmp, unsigned* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned s = lane < kStageThreads / 32 ? warp_tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kStageThreads / 32) warp_tmp[lane] = s;
+    }
+    __syncthreads();
+    const unsigned before = wid ? warp_tmp[wid - 1] : 0u;
+    *total = warp_tmp[kStageThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// 64-bit variant (warp_tmp must hold 8 u64).
+__device__ inline unsigned long long block_scan_u64(unsigned long long v, unsigned long long* warp_tmp,
+                                                    unsigned long long* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long s = lane < kStageThreads / 32 ? warp_tmp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kStageThreads / 32) warp_tmp[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long before = wid ? warp_tmp[wid - 1] : 0ull;
+    *total = warp_tmp[kStageThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+struct StageBufs {
+    unsigned long long* stage;   // S * W
+    unsigned long long* sorted;  // S * W
+    unsigned long long* gbase;   // P
+    unsigned* meta;              // S
+    unsigned* hist;              // P
+    unsigned* lbase;             // P
+    unsigned short* sorted_b;    // S
+    unsigned* warp_tmp;          // 8
+};
+
+__host__ __device__ inline size_t stage_smem_bytes(unsigned W, unsigned S, unsigned P) {
+    return (size_t)S * W * 8 * 2 + (size_t)P * 8 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
+}
+
+__device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigned S, unsigned P) {
+    StageBufs b;
+    b.stage = reinterpret_cast<unsigned long long*>(base);
+    b.sorted = b.stage + (size_t)S * W;
+    b.gbase = b.sorted + (size_t)S * W;
+    b.meta = reinterpret_cast<unsigned*>(b.gbase + P);
+    b.hist = b.meta + S;
+    b.lbase = b.hist + P;
+    b.sorted_b = reinterpret_cast<unsigned short*>(b.lbase + P);
+    b.warp_tmp = reinterpret_cast<unsigned*>(b.sorted_b + S + 8);  // 16-byte slack keeps it 4-aligned
+    return b;
+}
+
+// Flush one round.  meta[e] = (dest << 16) | rank for a staged record e, or
+// 0xFFFFFFFF; hist[d] = records staged for destination d.  Dest supplies
+// reserve(d, n) -> first slot index within d, start(d) -> record index of
+// slot 0 of d, cap(d) -> slots of d.  Records past cap are dropped and
+// reported through `status` (the host then retries with exact capacities).
+// hist is left zeroed for the next round.
+template <int W, class Dest>
+__device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
+                            unsigned* status, unsigned overflow_bit) {
+    __syncthreads();
+    // exclusive scan of hist -> lbase (each thread owns a run of consecutive destinations)
+    const unsigned per = (P + kStageThreads - 1) / kStageThreads;
+    const unsigned d0 = threadIdx.x * per;
+    unsigned mine = 0;
+    for (unsigned i = 0; i < per; ++i)
+        if (d0 + i < P) mine += b.hist[d0 + i];
+    unsigned total;
+    unsigned run = block_scan_u32(mine, b.warp_tmp, &total);
+    for (unsigned i = 0; i < per; ++i) {
+        const unsigned d = d0 + i;
+        if (d < P) {
+            const unsigned h = b.hist[d];
+            b.lbase[d] = run;
+            run += h;
+            if (h) b.gbase[d] = dest.reserve(d, h);
+        }
+    }
+    __syncthreads();
+    for (unsigned e = threadIdx.x; e < S; e += kStageThreads) {
+        const unsigned m = b.meta[e];
+        if (m != 0xFFFFFFFFu) {
+            const unsigned d = m >> 16;
+            const unsigned pos = b.lbase[d] + (m & 0xFFFFu);
+#pragma unroll
+            for (int w = 0; w < W; ++w) b.sorted[(size_t)pos * W + w] = b.stage[(size_t)e * W + w];
+            b.sorted_b[pos] = (unsigned short)d;
+        }
+    }
+    __syncthreads();
+    bool over = false;
+    for (unsigned pos = threadIdx.x; pos < total; pos += kStageThreads) {
+        const unsigned d = b.sorted_b[pos];
+        const unsigned long long g = b.gbase[d] + (pos - b.lbase[d]);
+        if (g < dest.cap(d)) {
+            const unsigned long long o = (dest.start(d) + g) * W;
+#pragma unroll
+            for (int w = 0; w < W; ++w) out_rec[o + w] = b.sorted[(size_t)pos * W + w];
+        } else {
+            over = true;
+        }
+    }
+    for (unsigned d = threadIdx.x; d < P; d += kStageThreads) b.hist[d] = 0;
+    if (over) atomicOr(status, overflow_bit);
+    __syncthreads();
+}
+
+}  // namespace kmer
