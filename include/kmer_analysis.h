@@ -97,8 +97,13 @@ typedef struct {
     uint64_t distinct_hint;  /* expected distinct canonical k-mers; 0 = assume every window distinct */
     uint64_t memory_budget;  /* device bytes the analysis may hold while querying; 0 = 85% of free memory */
     uint32_t leaf_bits;      /* tuning override: log2 of the number of partitions (0 = automatic) */
-    uint32_t reserved[5];    /* must be zero */
+    uint32_t flags;          /* KMER_FLAG_* */
+    uint32_t reserved[4];    /* must be zero */
 } kmer_analysis_params;
+
+/* flags: record CUDA events around each stage on the analysis stream and
+ * report the per-stage device times in kmer_analysis_stats. */
+#define KMER_FLAG_PROFILE 1u
 
 /* Results of the last query.  Device pointers owned by the analysis; valid
  * until the next submit, query, reset or destroy of the same handle. */
@@ -126,6 +131,12 @@ typedef struct {
     uint32_t variant;
     uint64_t device_bytes;      /* device memory held by the analysis */
     float ms_total;             /* wall time of the query, host clock */
+    uint32_t launches;          /* kernels launched by the query */
+    /* with KMER_FLAG_PROFILE: device time (CUDA events on the analysis
+     * stream) of each stage summed over passes and retries, and launches */
+    float ms_scatter, ms_repart, ms_leaf, ms_fallback;
+    uint32_t n_scatter, n_repart, n_leaf, n_fallback;
+    uint64_t records_l2;        /* records moved by the level-2 repartition */
 } kmer_analysis_stats;
 
 /* Fills *p with defaults: min_count 2, qual_offset 33, qual_threshold 20,
@@ -148,6 +159,13 @@ void kmer_analysis_default_params(kmer_analysis_params *p, uint32_t k);
 int kmer_readset_create(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
                         uint32_t qual_offset, uint32_t qual_threshold, int where, void *cuda_stream,
                         kmer_readset_t **out);
+/* Re-packs new reads into an existing readset (same arguments as
+ * kmer_readset_create, its qual_offset / qual_threshold are kept); device
+ * buffers are reused when large enough.  Synchronises the stream. */
+int kmer_readset_pack(kmer_readset_t *rs, const char *bases, const uint8_t *quals, const uint64_t *offsets,
+                      uint64_t n_reads, int where, void *cuda_stream);
+/* Kernels launched by the last create/pack of this readset. */
+int kmer_readset_launches(const kmer_readset_t *rs, uint32_t *launches);
 /* Number of reads and bases of a readset. */
 int kmer_readset_info(const kmer_readset_t *rs, uint64_t *n_reads, uint64_t *n_bases);
 /* Frees a readset.  It must not be submitted to an analysis that has not

@@ -35,6 +35,7 @@ KMER_HOST, KMER_DEVICE = 0, 1
 KMER_EXT_DEPTH_ADAPTIVE, KMER_EXT_STATIC = 0, 1
 KMER_VARIANT_PARTITIONED, KMER_VARIANT_HBM_TABLE = 0, 1
 KMER_CLS_FORK, KMER_CLS_DEAD_END = 4, 5
+KMER_FLAG_PROFILE = 1
 KMER_MAX_K = 127
 
 
@@ -50,7 +51,7 @@ class kmer_analysis_params(ctypes.Structure):
                 ("err_num", ctypes.c_uint32), ("err_den", ctypes.c_uint32), ("t_ext", ctypes.c_uint32),
                 ("variant", ctypes.c_uint32), ("distinct_hint", ctypes.c_uint64),
                 ("memory_budget", ctypes.c_uint64), ("leaf_bits", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
 
 
 class kmer_result_view(ctypes.Structure):
@@ -64,7 +65,11 @@ class kmer_analysis_stats(ctypes.Structure):
                 ("records_emitted", ctypes.c_uint64), ("passes", ctypes.c_uint32), ("pass_bits", ctypes.c_uint32),
                 ("l1_bits", ctypes.c_uint32), ("l2_bits", ctypes.c_uint32), ("retries", ctypes.c_uint32),
                 ("fallback_leaves", ctypes.c_uint32), ("leaf_table_slots", ctypes.c_uint32),
-                ("variant", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("ms_total", ctypes.c_float)]
+                ("variant", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("ms_total", ctypes.c_float),
+                ("launches", ctypes.c_uint32), ("ms_scatter", ctypes.c_float), ("ms_repart", ctypes.c_float),
+                ("ms_leaf", ctypes.c_float), ("ms_fallback", ctypes.c_float), ("n_scatter", ctypes.c_uint32),
+                ("n_repart", ctypes.c_uint32), ("n_leaf", ctypes.c_uint32), ("n_fallback", ctypes.c_uint32),
+                ("records_l2", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -75,6 +80,8 @@ _vp, _u32, _u64, _int = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctype
 _SIGNATURES = {
     "kmer_analysis_default_params": (None, [ctypes.POINTER(kmer_analysis_params), _u32]),
     "kmer_readset_create": (_int, [_vp, _vp, _vp, _u64, _u32, _u32, _int, _vp, ctypes.POINTER(_vp)]),
+    "kmer_readset_pack": (_int, [_vp, _vp, _vp, _vp, _u64, _int, _vp]),
+    "kmer_readset_launches": (_int, [_vp, ctypes.POINTER(_u32)]),
     "kmer_readset_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "kmer_readset_destroy": (_int, [_vp]),
     "kmer_analysis_create": (_int, [ctypes.POINTER(kmer_analysis_params), _vp, ctypes.POINTER(_vp)]),
@@ -131,6 +138,18 @@ def kmer_readset_create(bases: int, quals: int, offsets: int, n_reads: int, qual
     _check(load_library().kmer_readset_create(bases, quals, offsets, n_reads, qual_offset, qual_threshold,
                                               where, stream or None, ctypes.byref(out)), "kmer_readset_create")
     return out.value
+
+
+def kmer_readset_pack(rs: int, bases: int, quals: int, offsets: int, n_reads: int, where: int,
+                      stream: int = 0) -> None:
+    _check(load_library().kmer_readset_pack(rs, bases, quals, offsets, n_reads, where, stream or None),
+           "kmer_readset_pack")
+
+
+def kmer_readset_launches(rs: int) -> int:
+    n = _u32()
+    _check(load_library().kmer_readset_launches(rs, ctypes.byref(n)), "kmer_readset_launches")
+    return n.value
 
 
 def kmer_readset_info(rs: int) -> tuple[int, int]:
@@ -242,6 +261,15 @@ class ReadSet:
         self.handle = kmer_readset_create(_ptr(bases), _ptr(quals), _ptr(offsets), n, qual_offset,
                                           qual_threshold, where, _stream_of(stream))
         self.qual_offset, self.qual_threshold = qual_offset, qual_threshold
+
+    def pack(self, bases, quals, offsets, stream=None):
+        """Re-pack new reads into this readset, reusing its device buffers."""
+        kmer_readset_pack(self.handle, _ptr(bases), _ptr(quals), _ptr(offsets), len(offsets) - 1,
+                          _where(bases), _stream_of(stream))
+
+    @property
+    def launches(self) -> int:
+        return kmer_readset_launches(self.handle)
 
     @property
     def n_reads(self) -> int:

@@ -97,6 +97,8 @@ struct kmer_readset {
     unsigned long long n_reads = 0, n_bases = 0, n_blocks = 0;
     unsigned qual_offset = 33, qual_threshold = 20;
     DevBuf blocks, blk_off, offsets;
+    DevBuf tmp_bases, tmp_quals, nblk, scratch, stats;  // reused by re-packs
+    unsigned launches = 0;
     unsigned long long len_stats[kLenHist] = {};
 
     // Exact number of k-windows (before N filtering) for this k.
@@ -123,6 +125,10 @@ struct kmer_analysis {
     DevBuf fb_list, hbm, misc;
     unsigned long long out_cap = 0, fb_cap = 0;
     Misc* host_misc = nullptr;  // pinned
+    // profiling (KMER_FLAG_PROFILE): one begin/end event pair per stage
+    enum { STG_SCATTER, STG_REPART, STG_LEAF, STG_FALLBACK, STG_N };
+    cudaEvent_t ev_b[STG_N] = {}, ev_e[STG_N] = {};
+    bool ev_pending[STG_N] = {};
     // results
     bool have_result = false;
     unsigned long long n_out = 0, res_windows = 0, res_distinct = 0;
@@ -153,6 +159,7 @@ int validate_params(const kmer_analysis_params* p) {
     if (p->qual_offset > 255 || p->qual_threshold > 255)
         return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
     if (p->leaf_bits > 22) return fail(KMER_ERR_INVALID_ARG, "leaf_bits must be <= 22");
+    if (p->flags & ~KMER_FLAG_PROFILE) return fail(KMER_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
     for (unsigned r : p->reserved)
         if (r) return fail(KMER_ERR_INVALID_ARG, "reserved fields must be zero");
     return KMER_OK;
@@ -160,62 +167,77 @@ int validate_params(const kmer_analysis_params* p) {
 
 int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
                  uint64_t n_reads, int where, cudaStream_t s) {
-    rs->n_reads = n_reads;
+    rs->n_reads = 0;
+    rs->n_bases = 0;
+    rs->n_blocks = 0;
+    rs->launches = 0;
+    std::memset(rs->len_stats, 0, sizeof rs->len_stats);
     if (n_reads == 0) return KMER_OK;
     const char* d_bases = bases;
     const uint8_t* d_quals = quals;
-    const unsigned long long* d_off = reinterpret_cast<const unsigned long long*>(offsets);
-    DevBuf tmp_bases, tmp_quals;
     TRY(rs->offsets.ensure((n_reads + 1) * 8));
     if (where == KMER_HOST) {
         for (uint64_t i = 0; i < n_reads; ++i) {
-            if (offsets[i + 1] < offsets[i]) return fail(KMER_ERR_INVALID_ARG, "offsets decrease at read %llu", (unsigned long long)i);
+            if (offsets[i + 1] < offsets[i])
+                return fail(KMER_ERR_INVALID_ARG, "offsets decrease at read %llu", (unsigned long long)i);
             if (offsets[i + 1] - offsets[i] > 0xFFFFFFFFull)
                 return fail(KMER_ERR_INVALID_ARG, "read %llu is 2^32 bases or longer", (unsigned long long)i);
         }
         const unsigned long long nb = offsets[n_reads];
-        TRY(tmp_bases.ensure(nb + 16));
-        TRY(tmp_quals.ensure(nb + 16));
-        CK(cudaMemcpyAsync(tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
+        TRY(rs->tmp_bases.ensure(nb + 16));
+        TRY(rs->tmp_quals.ensure(nb + 16));
+        CK(cudaMemcpyAsync(rs->tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(rs->tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
-        d_bases = tmp_bases.as<char>();
-        d_quals = tmp_quals.as<uint8_t>();
+        d_bases = rs->tmp_bases.as<char>();
+        d_quals = rs->tmp_quals.as<uint8_t>();
     } else {
         CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyDeviceToDevice, s));
     }
-    d_off = rs->offsets.as<unsigned long long>();
+    const unsigned long long* d_off = rs->offsets.as<unsigned long long>();
     // read geometry: blocks per read, length histogram, monotonicity
-    DevBuf nblk, scratch, stats;
-    TRY(nblk.ensure(n_reads * 8));
+    TRY(rs->nblk.ensure(n_reads * 8));
     TRY(rs->blk_off.ensure((n_reads + 1) * 8));
-    TRY(scratch.ensure(scan_temp_bytes(n_reads)));
+    TRY(rs->scratch.ensure(scan_temp_bytes(n_reads)));
     const size_t stats_bytes = (kLenHist + 2) * 8;
-    TRY(stats.ensure(stats_bytes));
-    CK(cudaMemsetAsync(stats.p, 0, stats_bytes, s));
-    unsigned int* bad = reinterpret_cast<unsigned int*>(stats.as<unsigned long long>() + kLenHist);
-    CK(launch_read_geometry(d_off, n_reads, nblk.as<unsigned long long>(), stats.as<unsigned long long>(), bad, s));
-    CK(exclusive_scan_u64(nblk.as<unsigned long long>(), rs->blk_off.as<unsigned long long>(), n_reads, scratch.p, s));
-    std::vector<unsigned long long> host(kLenHist + 2);
-    CK(cudaMemcpyAsync(host.data(), stats.p, stats_bytes, cudaMemcpyDeviceToHost, s));
-    unsigned long long total_blocks = 0, first_off = 0, last_off = 0;
-    CK(cudaMemcpyAsync(&total_blocks, rs->blk_off.as<unsigned long long>() + n_reads, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&first_off, d_off, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&last_off, d_off + n_reads, 8, cudaMemcpyDeviceToHost, s));
+    TRY(rs->stats.ensure(stats_bytes + 3 * 8));
+    CK(cudaMemsetAsync(rs->stats.p, 0, stats_bytes, s));
+    unsigned long long* st = rs->stats.as<unsigned long long>();
+    unsigned int* bad = reinterpret_cast<unsigned int*>(st + kLenHist);
+    CK(launch_read_geometry(d_off, n_reads, rs->nblk.as<unsigned long long>(), st, bad, s));
+    CK(exclusive_scan_u64(rs->nblk.as<unsigned long long>(), rs->blk_off.as<unsigned long long>(), n_reads,
+                          rs->scratch.p, s));
+    // gather the totals next to the histogram so that one copy brings everything back
+    CK(cudaMemcpyAsync(st + kLenHist + 2, rs->blk_off.as<unsigned long long>() + n_reads, 8,
+                       cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(st + kLenHist + 3, d_off, 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(st + kLenHist + 4, d_off + n_reads, 8, cudaMemcpyDeviceToDevice, s));
+    std::vector<unsigned long long> host(kLenHist + 5);
+    CK(cudaMemcpyAsync(host.data(), st, host.size() * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const unsigned bad_flags = (unsigned)(host[kLenHist] & 0xFFFFFFFFull);
     if (bad_flags & 1u) return fail(KMER_ERR_INVALID_ARG, "offsets are not non-decreasing");
     if (bad_flags & 2u) return fail(KMER_ERR_INVALID_ARG, "a read is 2^32 bases or longer");
-    std::memcpy(rs->len_stats, host.data(), sizeof(rs->len_stats));
-    rs->n_blocks = total_blocks;
-    rs->n_bases = last_off - first_off;
+    const unsigned long long total_blocks = host[kLenHist + 2];
     TRY(rs->blocks.ensure(std::max<unsigned long long>(total_blocks, 1) * sizeof(PackedBlock)));
     int num_sms = 0;
     CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, rs->device));
     CK(launch_pack(d_bases, d_quals, d_off, rs->blk_off.as<unsigned long long>(), n_reads, rs->qual_offset,
                    rs->qual_threshold, rs->blocks.as<PackedBlock>(), num_sms, s));
     CK(cudaStreamSynchronize(s));
+    std::memcpy(rs->len_stats, host.data(), sizeof(rs->len_stats));
+    rs->n_blocks = total_blocks;
+    rs->n_bases = host[kLenHist + 4] - host[kLenHist + 3];
+    rs->n_reads = n_reads;
+    rs->launches = 5;  // geometry, three scan phases, pack
     return KMER_OK;
+}
+
+void destroy_readset(kmer_readset* rs) {
+    DevBuf* bs[] = {&rs->blocks, &rs->blk_off, &rs->offsets, &rs->tmp_bases, &rs->tmp_quals,
+                    &rs->nblk, &rs->scratch, &rs->stats};
+    for (auto* b : bs) b->release();
+    delete rs;
 }
 
 int make_readset(const char* bases, const uint8_t* quals, const uint64_t* offsets, uint64_t n_reads,
@@ -239,19 +261,18 @@ int make_readset(const char* bases, const uint8_t* quals, const uint64_t* offset
     rs->qual_threshold = qual_threshold;
     int rc = pack_readset(rs, bases, quals, offsets, n_reads, where, s);
     if (rc != KMER_OK) {
-        delete rs;
+        destroy_readset(rs);
         return rc;
     }
+    // a one-shot readset keeps only its packed form; kmer_readset_pack keeps staging for reuse
+    rs->tmp_bases.release();
+    rs->tmp_quals.release();
+    rs->nblk.release();
+    rs->scratch.release();
     *out = rs;
     return KMER_OK;
 }
 
-void destroy_readset(kmer_readset* rs) {
-    rs->blocks.release();
-    rs->blk_off.release();
-    rs->offsets.release();
-    delete rs;
-}
 
 // ------------------------------------------------------------------ planning
 struct Plan {
@@ -380,6 +401,41 @@ int status_error(unsigned st) {
     return KMER_OK;
 }
 
+bool profiling(const kmer_analysis* h) { return (h->p.flags & KMER_FLAG_PROFILE) != 0; }
+
+int prof_begin(kmer_analysis* h, int stg) {
+    if (!profiling(h)) return KMER_OK;
+    if (!h->ev_b[stg]) {
+        CK(cudaEventCreate(&h->ev_b[stg]));
+        CK(cudaEventCreate(&h->ev_e[stg]));
+    }
+    CK(cudaEventRecord(h->ev_b[stg], h->stream));
+    return KMER_OK;
+}
+
+int prof_end(kmer_analysis* h, int stg) {
+    if (!profiling(h)) return KMER_OK;
+    CK(cudaEventRecord(h->ev_e[stg], h->stream));
+    h->ev_pending[stg] = true;
+    return KMER_OK;
+}
+
+// After the stream was synchronised: add the elapsed time of finished stages.
+int prof_collect(kmer_analysis* h) {
+    if (!profiling(h)) return KMER_OK;
+    float* dst[] = {&h->st.ms_scatter, &h->st.ms_repart, &h->st.ms_leaf, &h->st.ms_fallback};
+    uint32_t* cnt[] = {&h->st.n_scatter, &h->st.n_repart, &h->st.n_leaf, &h->st.n_fallback};
+    for (int i = 0; i < kmer_analysis::STG_N; ++i) {
+        if (!h->ev_pending[i]) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev_b[i], h->ev_e[i]));
+        *dst[i] += ms;
+        *cnt[i] += 1;
+        h->ev_pending[i] = false;
+    }
+    return KMER_OK;
+}
+
 // HBM-table recount of the leaves listed by the leaf kernel.
 int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     if (n_fb == 0) return KMER_OK;
@@ -402,13 +458,17 @@ int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     const unsigned W = j.g.W;
     const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * max_n));
     TRY(h->hbm.ensure(cap * hbm_entry_bytes(W)));
+    TRY(prof_begin(h, kmer_analysis::STG_FALLBACK));
     for (unsigned lf : leaves) {
         const unsigned long long c = next_pow2(std::max<unsigned long long>(1024, 2 * fill[lf]));
         CK(cudaMemsetAsync(h->hbm.p, 0, c * hbm_entry_bytes(W), h->stream));
         CK(launch_records_insert(j, lf, h->hbm.p, c, h->num_sms, h->stream));
         CK(launch_hbm_sweep(j, h->hbm.p, c, h->num_sms, h->stream));
+        h->st.launches += 2;
     }
+    TRY(prof_end(h, kmer_analysis::STG_FALLBACK));
     TRY(read_misc(h));
+    TRY(prof_collect(h));
     return status_error(h->host_misc->status);
 }
 
@@ -472,22 +532,32 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             j.l2_leaf_start = exact_leaf.empty() ? nullptr : h->l2_leaf_start.as<unsigned long long>();
         }
         fill_job_outputs(h, j);
+        TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
         for (const kmer_readset* rs : h->submitted) {
             if (rs->n_reads == 0) continue;
             set_readset(j, rs);
             CK(launch_scatter(j, 0, rs->n_reads, h->stream));
+            h->st.launches++;
         }
+        TRY(prof_end(h, kmer_analysis::STG_SCATTER));
         // level 2 and leaves may be re-run without re-scattering
         for (unsigned sub_attempt = 0;; ++sub_attempt) {
             if (sub_attempt > 8) return fail(KMER_ERR_TABLE_FULL, "leaf buffers still too small after retries");
             if (g.p2) {
                 CK(cudaMemsetAsync(h->l2_fill.p, 0, P * 8ull, h->stream));
+                TRY(prof_begin(h, kmer_analysis::STG_REPART));
                 // exact leaf layout: the uniform capacities computed by the planner are unused
                 CK(launch_l2_plan(j, exact_leaf.empty() ? l2_capacity : ~0ull, h->stream));
                 CK(launch_repart(j, h->num_sms, h->stream));
+                TRY(prof_end(h, kmer_analysis::STG_REPART));
+                h->st.launches += 2;
             }
+            TRY(prof_begin(h, kmer_analysis::STG_LEAF));
             CK(launch_leaf(j, cap_max, h->stream));
+            TRY(prof_end(h, kmer_analysis::STG_LEAF));
+            h->st.launches++;
             TRY(read_misc(h));
+            TRY(prof_collect(h));
             const Misc m = *h->host_misc;
             if (m.status & ST_L1_OVERFLOW) break;  // re-scatter with exact bucket sizes
             if (m.status & ST_L2_OVERFLOW) {
@@ -527,6 +597,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             h->res_windows += fin.stats[0];
             h->res_distinct += fin.stats[1];
             h->st.records_emitted += fin.stats[2];
+            if (g.p2) h->st.records_l2 += fin.stats[2];
             return KMER_OK;
         }
         // level-1 overflow: take the exact bucket demand and re-scatter
@@ -556,13 +627,20 @@ int run_direct(kmer_analysis* h, unsigned long long windows) {
         Job j{};
         j.g = g;
         fill_job_outputs(h, j);
+        TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
         for (const kmer_readset* rs : h->submitted) {
             if (rs->n_reads == 0) continue;
             set_readset(j, rs);
             CK(launch_direct_insert(j, h->hbm.p, cap, h->stream));
+            h->st.launches++;
         }
+        TRY(prof_end(h, kmer_analysis::STG_SCATTER));
+        TRY(prof_begin(h, kmer_analysis::STG_LEAF));
         CK(launch_hbm_sweep(j, h->hbm.p, cap, h->num_sms, h->stream));
+        TRY(prof_end(h, kmer_analysis::STG_LEAF));
+        h->st.launches++;
         TRY(read_misc(h));
+        TRY(prof_collect(h));
         const Misc m = *h->host_misc;
         if ((m.status & ST_TABLE_FULL) && attempt < 6) {
             cap *= 2;
@@ -664,6 +742,22 @@ int kmer_readset_create(const char* bases, const uint8_t* quals, const uint64_t*
                         kmer_readset_t** out) {
     return make_readset(bases, quals, offsets, n_reads, qual_offset, qual_threshold, where,
                         static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+int kmer_readset_pack(kmer_readset_t* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
+                      uint64_t n_reads, int where, void* cuda_stream) {
+    if (!rs) return fail(KMER_ERR_INVALID_ARG, "readset is NULL");
+    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (n_reads && (!bases || !quals || !offsets))
+        return fail(KMER_ERR_INVALID_ARG, "bases, quals and offsets must be non-NULL when n_reads > 0");
+    DeviceGuard dg(rs->device);
+    return pack_readset(rs, bases, quals, offsets, n_reads, where, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int kmer_readset_launches(const kmer_readset_t* rs, uint32_t* launches) {
+    if (!rs || !launches) return fail(KMER_ERR_INVALID_ARG, "NULL readset or output");
+    *launches = rs->launches;
+    return KMER_OK;
 }
 
 int kmer_readset_info(const kmer_readset_t* rs, uint64_t* n_reads, uint64_t* n_bases) {
@@ -806,6 +900,10 @@ int kmer_analysis_destroy(kmer_analysis_t* h) {
                     &h->out_cls, &h->fb_list, &h->hbm, &h->misc};
     for (auto* b : bs) b->release();
     if (h->host_misc) cudaFreeHost(h->host_misc);
+    for (int i = 0; i < kmer_analysis::STG_N; ++i) {
+        if (h->ev_b[i]) cudaEventDestroy(h->ev_b[i]);
+        if (h->ev_e[i]) cudaEventDestroy(h->ev_e[i]);
+    }
     delete h;
     return KMER_OK;
 }
