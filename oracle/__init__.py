@@ -71,6 +71,11 @@ def _load():
             lib.oracle_free.restype = None
             lib.oracle_fnv1a.argtypes = [ctypes.c_char_p, ctypes.c_uint64]
             lib.oracle_fnv1a.restype = ctypes.c_uint64
+            lib.oracle_count_keys.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(_Params), vp,
+                                              ctypes.c_uint64, vp, vp]
+            lib.oracle_count_keys.restype = ctypes.c_int
+            lib.oracle_classify.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_Params), vp]
+            lib.oracle_classify.restype = None
             _lib = lib
     return _lib
 
@@ -167,3 +172,45 @@ def run_shards(bases, quals, offsets, params: Params, shards, n_shards: int, thr
 def fnv1a(key: bytes) -> int:
     """The oracle's shard hash (FNV-1a, 64 bit) of one key string."""
     return int(_load().oracle_fnv1a(key, len(key)))
+
+
+def count_keys(bases, quals, offsets, params: Params, keys: np.ndarray, threads: int = 1):
+    """The definition restricted to the canonical keys `keys` (dtype S{k}):
+    returns count (n,), ext (n, 8) and cls (n, 2) over all reads.  The reads
+    are split into `threads` contiguous ranges counted in parallel and summed."""
+    lib = _load()
+    b = _as_u8(bases)
+    q = _as_u8(quals)
+    o = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n_reads = len(o) - 1
+    keys = np.ascontiguousarray(keys, dtype=f"S{params.k}")
+    n = len(keys)
+    cp = params._c()
+    cuts = np.linspace(0, n_reads, max(1, threads) + 1).astype(np.int64)
+    parts = []
+
+    def work(i):
+        a, e = int(cuts[i]), int(cuts[i + 1])
+        cnt = np.zeros(n, dtype=np.uint64)
+        ext = np.zeros((n, 8), dtype=np.uint64)
+        sub = np.ascontiguousarray(o[a:e + 1])
+        rc = lib.oracle_count_keys(ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(q.ctypes.data),
+                                   ctypes.c_void_p(sub.ctypes.data), e - a, ctypes.byref(cp),
+                                   ctypes.c_void_p(keys.ctypes.data), n, ctypes.c_void_p(cnt.ctypes.data),
+                                   ctypes.c_void_p(ext.ctypes.data))
+        if rc:
+            raise ValueError("oracle_count_keys rejected its arguments")
+        return cnt, ext
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        parts = list(ex.map(work, range(len(cuts) - 1)))
+    count = sum(p[0] for p in parts)
+    ext = sum(p[1] for p in parts)
+    cls = np.zeros((n, 2), dtype=np.uint8)
+    for i in range(n):
+        e8 = np.ascontiguousarray(ext[i])
+        out = np.zeros(2, dtype=np.uint8)
+        lib.oracle_classify(ctypes.c_void_p(e8.ctypes.data), int(count[i]), ctypes.byref(cp),
+                            ctypes.c_void_p(out.ctypes.data))
+        cls[i] = out
+    return count, ext, cls

@@ -138,6 +138,42 @@ uint8_t classify(const uint64_t n[4], uint64_t d, const oracle_params &p) {
     return lhs <= (a > b ? a : b) ? (uint8_t)m : FORK;
 }
 
+// Walk every window of one read; for each window without N call
+// visit(canonical key, left base/quality/exists, right base/quality/exists)
+// with the extensions already in the key's orientation.
+template <class Visit>
+void walk_read(const std::string &read, const uint8_t *q, size_t k, const oracle_params &p, Visit visit) {
+    const size_t L = read.size();
+    for (size_t i = 0; i + k <= L; ++i) {
+        std::string w = read.substr(i, k);
+        bool ok = true;
+        for (char c : w)
+            if (base_index(c) < 0) ok = false;
+        if (!ok) continue;
+        std::string u = reverse_complement(w);
+        bool flip = u < w;
+        // candidate extensions in read orientation
+        bool has_l = i > 0, has_r = i + k < L;
+        char lb = has_l ? read[i - 1] : 'N', rb = has_r ? read[i + k] : 'N';
+        int lq = has_l ? (int)q[i - 1] - p.qual_offset : -1;
+        int rq = has_r ? (int)q[i + k] - p.qual_offset : -1;
+        if (flip) {  // the stored key reads the other strand
+            char nl = complement(rb), nr = complement(lb);
+            int nlq = rq, nrq = lq;
+            bool nhl = has_r, nhr = has_l;
+            lb = nl; rb = nr; lq = nlq; rq = nrq; has_l = nhl; has_r = nhr;
+        }
+        visit(flip ? u : w, has_l && base_index(lb) >= 0 && lq >= p.qual_threshold ? base_index(lb) : -1,
+              has_r && base_index(rb) >= 0 && rq >= p.qual_threshold ? base_index(rb) : -1);
+    }
+}
+
+void add_window(Rec &rec, int left, int right) {
+    rec.count += 1;
+    if (left >= 0) rec.ext[0][left] += 1;
+    if (right >= 0) rec.ext[1][right] += 1;
+}
+
 }  // namespace
 
 extern "C" int oracle_kmer_analysis(const char *bases, const uint8_t *quals, const uint64_t *offsets,
@@ -152,35 +188,11 @@ extern "C" int oracle_kmer_analysis(const char *bases, const uint8_t *quals, con
     uint64_t windows = 0;
     for (uint64_t r = 0; r < n_reads; ++r) {
         const std::string read(bases + offsets[r], bases + offsets[r + 1]);
-        const uint8_t *q = quals + offsets[r];
-        const size_t L = read.size();
-        for (size_t i = 0; i + k <= L; ++i) {
-            std::string w = read.substr(i, k);
-            bool ok = true;
-            for (char c : w)
-                if (base_index(c) < 0) ok = false;
-            if (!ok) continue;
-            std::string u = reverse_complement(w);
-            bool flip = u < w;
-            const std::string &c = flip ? u : w;
-            if (n_shards > 1 && fnv1a(c) % n_shards != shard) continue;
+        walk_read(read, quals + offsets[r], k, *p, [&](const std::string &c, int left, int right) {
+            if (n_shards > 1 && fnv1a(c) % n_shards != shard) return;
             ++windows;
-            // candidate extensions in read orientation
-            bool has_l = i > 0, has_r = i + k < L;
-            char lb = has_l ? read[i - 1] : 'N', rb = has_r ? read[i + k] : 'N';
-            int lq = has_l ? (int)q[i - 1] - p->qual_offset : -1;
-            int rq = has_r ? (int)q[i + k] - p->qual_offset : -1;
-            if (flip) {  // the stored key reads the other strand
-                char nl = complement(rb), nr = complement(lb);
-                int nlq = rq, nrq = lq;
-                bool nhl = has_r, nhr = has_l;
-                lb = nl; rb = nr; lq = nlq; rq = nrq; has_l = nhl; has_r = nhr;
-            }
-            Rec &rec = M[c];
-            rec.count += 1;
-            if (has_l && base_index(lb) >= 0 && lq >= p->qual_threshold) rec.ext[0][base_index(lb)] += 1;
-            if (has_r && base_index(rb) >= 0 && rq >= p->qual_threshold) rec.ext[1][base_index(rb)] += 1;
-        }
+            add_window(M[c], left, right);
+        });
     }
     std::vector<const std::pair<const std::string, Rec> *> keep;
     for (const auto &kv : M)
@@ -218,4 +230,39 @@ extern "C" void oracle_free(oracle_result *r) {
 
 extern "C" uint64_t oracle_fnv1a(const char *s, uint64_t len) {
     return fnv1a(std::string(s, s + len));
+}
+
+/* The same definition restricted to an explicit set of canonical keys
+ * (n_keys strings of k characters, each the smaller of itself and its
+ * reverse complement): count[i], ext[8i..8i+8) and cls[2i..2i+2) of key i,
+ * accumulated over the given reads.  Counts add across calls on disjoint
+ * read ranges (update-only inserts commute, Sec. II-A use case 1), so a
+ * caller may split the reads over threads and sum. */
+extern "C" int oracle_count_keys(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
+                                 const oracle_params *p, const char *keys, uint64_t n_keys, uint64_t *count,
+                                 uint64_t *ext) {
+    if (!p || (n_reads && (!bases || !quals || !offsets)) || (n_keys && (!keys || !count || !ext))) return -1;
+    const size_t k = p->k;
+    std::map<std::string, uint64_t> index;
+    for (uint64_t i = 0; i < n_keys; ++i) index[std::string(keys + i * k, keys + (i + 1) * k)] = i;
+    std::vector<Rec> recs(n_keys);
+    for (uint64_t r = 0; r < n_reads; ++r) {
+        const std::string read(bases + offsets[r], bases + offsets[r + 1]);
+        walk_read(read, quals + offsets[r], k, *p, [&](const std::string &c, int left, int right) {
+            auto it = index.find(c);
+            if (it != index.end()) add_window(recs[it->second], left, right);
+        });
+    }
+    for (uint64_t i = 0; i < n_keys; ++i) {
+        count[i] += recs[i].count;
+        for (int s = 0; s < 2; ++s)
+            for (int b = 0; b < 4; ++b) ext[8 * i + 4 * s + b] += recs[i].ext[s][b];
+    }
+    return 0;
+}
+
+/* Classes of one k-mer from its summed tallies (the rule of oracle_kmer_analysis). */
+extern "C" void oracle_classify(const uint64_t *ext8, uint64_t count, const oracle_params *p, uint8_t *cls2) {
+    cls2[0] = classify(ext8, count, *p);
+    cls2[1] = classify(ext8 + 4, count, *p);
 }

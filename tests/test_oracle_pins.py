@@ -348,3 +348,20 @@ def test_generator_ground_truth(k):
     res = oracle.run(rs.bases, rs.quals, rs.offsets, oracle.Params(k=k, min_count=1))
     got = {row[0]: [row[1], row[2]] for row in as_rows(res)}
     assert got == truth
+
+
+def test_count_keys_matches_full_definition():
+    """The key-set mode equals the full oracle restricted to those keys, for any
+    split of the reads over threads; keys never seen get zero counts."""
+    rs = small_metagenome(n_reads=2500, seed=5)
+    for k in (21, 33):
+        p = oracle.Params(k=k, min_count=1)
+        full = oracle.run(rs.bases, rs.quals, rs.offsets, p)
+        idx = np.random.default_rng(k).choice(len(full), 200, replace=False)
+        for threads in (1, 3):
+            c, e, cl = oracle.count_keys(rs.bases, rs.quals, rs.offsets, p, full.keys[idx], threads=threads)
+            assert (c == full.count[idx]).all() and (e == full.ext[idx]).all() and (cl == full.cls[idx]).all()
+        absent = np.array([b"A" * k], dtype=f"S{k}")
+        if absent[0] not in set(full.keys):
+            c, e, cl = oracle.count_keys(rs.bases, rs.quals, rs.offsets, p, absent, threads=2)
+            assert c[0] == 0 and (e == 0).all() and tuple(cl[0]) == (oracle.DEAD_END, oracle.DEAD_END)
