@@ -133,6 +133,11 @@ struct kmer_analysis {
     bool have_result = false;
     unsigned long long n_out = 0, res_windows = 0, res_distinct = 0;
     unsigned long long out_hint = 0;  // survivors of the previous query (buffer sizing)
+    // sizing learned from earlier queries: distinct / windows at this k, and the
+    // level-2 leaf slack (grown whenever a leaf overflowed)
+    unsigned hist_k = 0;
+    double hist_ratio = 0.0;
+    unsigned l2_slack_num = 384;  // 1.5 * mean
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -289,8 +294,10 @@ Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget
     g.hb = 2 * g.k - 64 * (g.W - 1);
     g.bt = g.W == 1 ? 2 * g.k : 64;
     pl.windows = windows;
-    const unsigned long long basis = h->p.distinct_hint ? std::min<unsigned long long>(h->p.distinct_hint, windows)
-                                                        : windows;
+    unsigned long long basis = windows;
+    if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
+    else if (h->hist_k == h->p.k && h->hist_ratio > 0.0)  // learned from the previous query at this k
+        basis = std::min<unsigned long long>(windows, (unsigned long long)(1.15 * h->hist_ratio * (double)windows) + 1);
     const unsigned long long target = std::max(64u, cap_max / 2);
     unsigned p = h->p.leaf_bits ? h->p.leaf_bits : ceil_log2((basis + target - 1) / target);
     const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
@@ -376,6 +383,11 @@ void fill_job_outputs(kmer_analysis* h, Job& j) {
     j.err_num = h->p.err_num;
     j.err_den = h->p.err_den;
     j.t_ext = h->p.t_ext;
+    j.l2_slack_num = h->l2_slack_num;
+    // leaf table: twice the expected distinct keys of a leaf (one slot per record if unknown)
+    double ratio = 1.0;
+    if (h->hist_k == h->p.k && h->hist_ratio > 0.0) ratio = std::min(1.0, 2.0 * h->hist_ratio + 0.05);
+    j.table_ratio_num = (unsigned)(ratio * 65536.0);
 }
 
 void set_readset(Job& j, const kmer_readset* rs) {
@@ -553,7 +565,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
                 h->st.launches += 2;
             }
             TRY(prof_begin(h, kmer_analysis::STG_LEAF));
-            CK(launch_leaf(j, cap_max, h->stream));
+            CK(launch_leaf(j, cap_max, h->num_sms, h->stream));
             TRY(prof_end(h, kmer_analysis::STG_LEAF));
             h->st.launches++;
             TRY(read_misc(h));
@@ -564,6 +576,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
                 std::vector<unsigned long long> fill(P);
                 CK(cudaMemcpyAsync(fill.data(), h->l2_fill.p, P * 8ull, cudaMemcpyDeviceToHost, h->stream));
                 CK(cudaStreamSynchronize(h->stream));
+                h->l2_slack_num = std::min(4096u, h->l2_slack_num * 3 / 2);  // future queries: more slack
                 exact_leaf.assign(P + 1, 0);
                 for (unsigned i = 0; i < P; ++i) exact_leaf[i + 1] = exact_leaf[i] + fill[i];
                 l2_capacity = exact_leaf[P];
@@ -697,6 +710,10 @@ int do_query(kmer_analysis* h) {
         }
     }
     h->out_hint = h->n_out;
+    if (h->res_windows) {
+        h->hist_k = h->p.k;
+        h->hist_ratio = (double)h->res_distinct / (double)h->res_windows;
+    }
     h->st.windows = h->res_windows;
     h->st.distinct = h->res_distinct;
     h->st.survivors = h->n_out;

@@ -59,10 +59,8 @@ __host__ __device__ constexpr unsigned long long inv_odd(unsigned long long c) {
     return x;
 }
 constexpr unsigned long long kM1 = 0xBF58476D1CE4E5B9ull;
-constexpr unsigned long long kM2 = 0x94D049BB133111EBull;
 constexpr unsigned long long kM1i = inv_odd(kM1);
-constexpr unsigned long long kM2i = inv_odd(kM2);
-static_assert(kM1 * kM1i == 1ull && kM2 * kM2i == 1ull, "odd inverses");
+static_assert(kM1 * kM1i == 1ull, "odd inverse");
 
 __host__ __device__ inline unsigned long long low_mask(unsigned b) {
     return b >= 64 ? ~0ull : ((1ull << b) - 1ull);
@@ -75,23 +73,21 @@ __host__ __device__ inline unsigned long long unxorshift(unsigned long long y, u
     return x;
 }
 
-// A bijection on b-bit integers (2 <= b <= 64): xorshift-multiply rounds,
-// each invertible on b bits (splitmix64 finalizer shape, constants shared).
+// A bijection on b-bit integers (2 <= b <= 64): xorshift, multiply by an odd
+// constant mod 2^b, xorshift -- each step invertible on b bits.  The top bits
+// of z (partition) depend on every key bit through the multiply's carries;
+// the final xorshift folds them back into the low bits (table slot).
 __host__ __device__ inline unsigned long long mix_bits(unsigned long long x, unsigned b) {
     const unsigned long long m = low_mask(b);
     const unsigned s = b > 2 ? (b + 1) / 2 : 1;
     x ^= x >> s;
     x = (x * kM1) & m;
     x ^= x >> s;
-    x = (x * kM2) & m;
-    x ^= x >> s;
     return x;
 }
 __host__ __device__ inline unsigned long long unmix_bits(unsigned long long z, unsigned b) {
     const unsigned long long m = low_mask(b);
     const unsigned s = b > 2 ? (b + 1) / 2 : 1;
-    z = unxorshift(z, s) & m;
-    z = (z * kM2i) & m;
     z = unxorshift(z, s) & m;
     z = (z * kM1i) & m;
     z = unxorshift(z, s) & m;
@@ -104,7 +100,12 @@ template <int W>
 __host__ __device__ inline unsigned long long head_hash(const unsigned long long (&w)[W]) {
     unsigned long long h = 0x9E3779B97F4A7C15ull;
 #pragma unroll
-    for (int i = 0; i < W - 1; ++i) h = mix_bits(h ^ w[i], 64);
+    for (int i = 0; i < W - 1; ++i) {
+        h ^= w[i];
+        h ^= h >> 31;
+        h *= 0x94D049BB133111EBull;
+        h ^= h >> 29;
+    }
     return W > 1 ? h : 0ull;
 }
 
@@ -165,6 +166,10 @@ struct Job {
     unsigned int fb_cap;
     // classification
     unsigned min_count, ext_mode, t_base, err_num, err_den, t_ext;
+    // sizing: level-2 leaf capacity = mean * l2_slack_num / 256 + 256 records;
+    // leaf table slots = records * table_ratio_num / 65536 + 512 (capped)
+    unsigned l2_slack_num;
+    unsigned table_ratio_num;
     // status and statistics
     unsigned int* status;
     unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted

@@ -32,7 +32,7 @@ cudaError_t launch_repart(const Job& j, int num_sms, cudaStream_t s);
 // a4-a7 fused: count each leaf in shared memory, filter, classify, compact.
 unsigned leaf_table_cap(unsigned W, size_t smem_budget);
 size_t leaf_smem_bytes(unsigned W, unsigned cap);
-cudaError_t launch_leaf(const Job& j, unsigned cap_max, cudaStream_t s);
+cudaError_t launch_leaf(const Job& j, unsigned cap_max, int num_sms, cudaStream_t s);
 
 // HBM open-addressing table (direct variant and fallback for leaves that do
 // not fit on chip).  Entries are zeroed by the caller (cudaMemsetAsync 0).

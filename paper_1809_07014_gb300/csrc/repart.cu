@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kStageThreads) l2_plan_kernel(const Job j, uns
             n = f < c ? f : c;
             tiles = (n + tile - 1) / tile;
             const unsigned long long mean = (n + P2 - 1) / P2;
-            const unsigned long long lc = n ? mean + mean / 4 + 64 : 0;
+            const unsigned long long lc = n ? (mean * j.l2_slack_num >> 8) + 256 : 0;
             leafcap = lc > 0xFFFFFFF0ull ? 0xFFFFFFF0u : (unsigned)lc;
             slots = (unsigned long long)leafcap * P2;
         }
@@ -101,17 +101,25 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job j) {
         const unsigned long long begin = (tile - j.tile_prefix[bucket]) * S;
         const unsigned cnt = (unsigned)(n - begin < S ? n - begin : S);
         const unsigned long long* src = j.l1_rec + (j.l1_start[bucket] + begin) * W;
-        for (unsigned e = threadIdx.x; e < S; e += kStageThreads) {
+        // all of this thread's records of the tile are requested before any is used
+        constexpr unsigned U = S / kStageThreads;
+        unsigned long long rec[U][W];
+#pragma unroll
+        for (unsigned u = 0; u < U; ++u) {
+            const unsigned e = u * kStageThreads + threadIdx.x;
+#pragma unroll
+            for (int w = 0; w < W; ++w) rec[u][w] = e < cnt ? __ldcs(src + (size_t)e * W + w) : 0ull;
+        }
+#pragma unroll
+        for (unsigned u = 0; u < U; ++u) {
+            const unsigned e = u * kStageThreads + threadIdx.x;
             unsigned m = 0xFFFFFFFFu;
             if (e < cnt) {
-                unsigned long long rec[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) rec[w] = __ldcs(src + (size_t)e * W + w);
-                const unsigned long long zl = rec[W - 1] >> 6;
+                const unsigned long long zl = rec[u][W - 1] >> 6;
                 const unsigned sub = (unsigned)(zl >> (zb - j.g.p2)) & (P2 - 1u);
                 const unsigned rank = atomicAdd(&b.hist[sub], 1u);
 #pragma unroll
-                for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[w];
+                for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[u][w];
                 m = (sub << 16) | rank;
             }
             b.meta[e] = m;

@@ -17,6 +17,7 @@ struct Roll {
     long long last_n;             // last position holding an N (or -1)
     unsigned long long cur;       // bases of the current block, next base in the top 2 bits
     unsigned curn, curg;          // N / good bits of the current block, next base in bit 0
+    uint4 nxt;                    // the block after the current one, loaded one block ahead
     unsigned out;                 // base that left the window at the last step
     const PackedBlock* blk;
     unsigned long long L;
@@ -37,6 +38,7 @@ struct Roll {
         out = 0;
         cur = 0;
         curn = curg = 0;
+        nxt = L ? __ldg(reinterpret_cast<const uint4*>(blk)) : make_uint4(0, 0, 0, 0);
     }
 
     // Step t (0 <= t <= L).  First the window [t-k, t) is reported if t >= k
@@ -47,10 +49,10 @@ struct Roll {
         unsigned b = 0, good = 0, isn = 0;
         if (t < L) {
             if ((t & 31) == 0) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4*>(blk + (t >> 5)));
-                cur = ((unsigned long long)v.y << 32) | v.x;
-                curn = v.z;
-                curg = v.w;
+                cur = ((unsigned long long)nxt.y << 32) | nxt.x;
+                curn = nxt.z;
+                curg = nxt.w;
+                if (t + 32 < L) nxt = __ldg(reinterpret_cast<const uint4*>(blk + (t >> 5) + 1));
             }
             b = (unsigned)(cur >> 62);
             cur <<= 2;

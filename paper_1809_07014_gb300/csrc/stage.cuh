@@ -10,6 +10,7 @@
 namespace kmer {
 
 constexpr int kStageThreads = 256;
+constexpr unsigned kMaxStageDest = 2048;  // destinations of one staging round (partition fan-out)
 
 // Exclusive scan across the 256 threads of the block (all must call).
 __device__ inline unsigned block_scan_u32(unsigned v, unsigned* warp_tmp, unsigned* total) {
@@ -69,7 +70,8 @@ __device__ inline unsigned long long block_scan_u64(unsigned long long v, unsign
 struct StageBufs {
     unsigned long long* stage;   // S * W
     unsigned long long* sorted;  // S * W
-    unsigned long long* gbase;   // P
+    unsigned long long* wbase;   // P: record index of sorted position 0 of destination d
+    unsigned long long* limit;   // P: first record index past destination d
     unsigned* meta;              // S
     unsigned* hist;              // P
     unsigned* lbase;             // P
@@ -78,15 +80,16 @@ struct StageBufs {
 };
 
 __host__ __device__ inline size_t stage_smem_bytes(unsigned W, unsigned S, unsigned P) {
-    return (size_t)S * W * 8 * 2 + (size_t)P * 8 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
+    return (size_t)S * W * 8 * 2 + (size_t)P * 16 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
 }
 
 __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigned S, unsigned P) {
     StageBufs b;
     b.stage = reinterpret_cast<unsigned long long*>(base);
     b.sorted = b.stage + (size_t)S * W;
-    b.gbase = b.sorted + (size_t)S * W;
-    b.meta = reinterpret_cast<unsigned*>(b.gbase + P);
+    b.wbase = b.sorted + (size_t)S * W;
+    b.limit = b.wbase + P;
+    b.meta = reinterpret_cast<unsigned*>(b.limit + P);
     b.hist = b.meta + S;
     b.lbase = b.hist + P;
     b.sorted_b = reinterpret_cast<unsigned short*>(b.lbase + P);
@@ -112,13 +115,21 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
         if (d0 + i < P) mine += b.hist[d0 + i];
     unsigned total;
     unsigned run = block_scan_u32(mine, b.warp_tmp, &total);
-    for (unsigned i = 0; i < per; ++i) {
+    // reservations of this thread's destinations are independent: unrolled so
+    // that all of them are in flight together
+    constexpr unsigned kMaxPer = kMaxStageDest / kStageThreads;
+#pragma unroll
+    for (unsigned i = 0; i < kMaxPer; ++i) {
         const unsigned d = d0 + i;
-        if (d < P) {
+        if (i < per && d < P) {
             const unsigned h = b.hist[d];
             b.lbase[d] = run;
+            if (h) {
+                const unsigned long long st = dest.start(d);
+                b.wbase[d] = st + dest.reserve(d, h) - run;
+                b.limit[d] = st + dest.cap(d);
+            }
             run += h;
-            if (h) b.gbase[d] = dest.reserve(d, h);
         }
     }
     __syncthreads();
@@ -136,11 +147,10 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     bool over = false;
     for (unsigned pos = threadIdx.x; pos < total; pos += kStageThreads) {
         const unsigned d = b.sorted_b[pos];
-        const unsigned long long g = b.gbase[d] + (pos - b.lbase[d]);
-        if (g < dest.cap(d)) {
-            const unsigned long long o = (dest.start(d) + g) * W;
+        const unsigned long long g = b.wbase[d] + pos;
+        if (g < b.limit[d]) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) out_rec[o + w] = b.sorted[(size_t)pos * W + w];
+            for (int w = 0; w < W; ++w) out_rec[g * W + w] = b.sorted[(size_t)pos * W + w];
         } else {
             over = true;
         }
