@@ -212,6 +212,32 @@ int kmer_analysis_reset(kmer_analysis_t *h);
 /* Releases the analysis and every buffer it owns.  NULL is accepted. */
 int kmer_analysis_destroy(kmer_analysis_t *h);
 
+/* k-mer analysis without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code that runs inside an allocator or memory-pool hook and
+ * must not re-enter it, plugins whose host application owns every device
+ * allocation, and paths where an allocation (with the synchronisation it can
+ * imply) is not allowed.  It computes the same result as kmer_analysis_query
+ * (variant KMER_VARIANT_HBM_TABLE) for one batch of reads given as DEVICE
+ * pointers (bases, quals, offsets as in kmer_readset_create), with only
+ * k, min_count, qual_offset, qual_threshold and the classification fields of
+ * *p used.  Its only device scratch is a 32 MiB array at file scope, reserved
+ * on each device where the library is used and held until the process exits;
+ * it bounds the input: the reads may span at most 393216 bases for k <= 63
+ * and 196608 bases for k >= 65 (larger inputs return INVALID_ARG before any
+ * work).  The caller passes the output arrays (device pointers, `capacity`
+ * k-mers, layout of kmer_result_view); *n_out receives the number of
+ * survivors, and if it exceeds `capacity` the call returns INVALID_ARG with
+ * the surplus not written.  Synchronises `cuda_stream`.  The first call on a
+ * device also looks up the scratch array's device address, so make that
+ * first call before any stream capture.  Every call reuses the same array
+ * (each call clears it first): calls that overlap on the GPU, from several
+ * streams or threads, race and must be serialised by the caller.  Errors:
+ * INVALID_ARG, NO_DEVICE, TABLE_FULL, COUNTER_OVERFLOW, TIMEOUT, CUDA. */
+int kmer_analysis_run_noalloc(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
+                              const kmer_analysis_params *p, uint64_t *keys, uint32_t *count, uint32_t *ext,
+                              uint8_t *cls, uint64_t capacity, uint64_t *n_out, void *cuda_stream);
+
 /* Static description of an error code. */
 const char *kmer_strerror(int code);
 

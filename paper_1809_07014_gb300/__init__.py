@@ -92,6 +92,8 @@ _SIGNATURES = {
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
+    "kmer_analysis_run_noalloc": (_int, [_vp, _vp, _vp, _u64, ctypes.POINTER(kmer_analysis_params), _vp, _vp, _vp,
+                                         _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "kmer_strerror": (ctypes.c_char_p, [_int]),
     "kmer_last_error_message": (ctypes.c_char_p, []),
     "kmer_version": (ctypes.c_char_p, []),
@@ -201,6 +203,16 @@ def kmer_analysis_reset(h: int) -> None:
 
 def kmer_analysis_destroy(h: int) -> None:
     _check(load_library().kmer_analysis_destroy(h), "kmer_analysis_destroy")
+
+
+def kmer_analysis_run_noalloc(bases: int, quals: int, offsets: int, n_reads: int, params: kmer_analysis_params,
+                              keys: int, count: int, ext: int, cls: int, capacity: int, stream: int = 0) -> int:
+    """Run the allocation-free entry point; returns the number of survivors."""
+    n = _u64()
+    _check(load_library().kmer_analysis_run_noalloc(bases, quals, offsets, n_reads, ctypes.byref(params), keys,
+                                                    count, ext, cls, capacity, ctypes.byref(n), stream or None),
+           "kmer_analysis_run_noalloc")
+    return n.value
 
 
 def kmer_strerror(code: int) -> str:
