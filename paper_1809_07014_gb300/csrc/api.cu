@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -137,7 +138,7 @@ struct kmer_analysis {
     // level-2 leaf slack (grown whenever a leaf overflowed)
     unsigned hist_k = 0;
     double hist_ratio = 0.0;
-    unsigned l2_slack_num = 384;  // 1.5 * mean
+    unsigned l2_slack_num = 512;  // leaf capacity = 2 * mean + 256
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -318,7 +319,12 @@ Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget
         p1 = lb;
         p2 = 0;
     } else {
-        p1 = std::min(11u, (lb + 1) / 2);
+        // the scatter's cost grows with its fan-out more than the repartition's does
+        p1 = std::min(11u, lb / 2);
+        if (const char* e = getenv("KMER_L1_BITS")) {  // tuning experiments only
+            const int v = atoi(e);
+            if (v >= 1 && v <= 11 && (unsigned)v < lb) p1 = (unsigned)v;
+        }
         p2 = lb - p1;
         if (p2 > 11) { p2 = 11; }
     }
@@ -397,10 +403,12 @@ void set_readset(Job& j, const kmer_readset* rs) {
     j.n_reads = rs->n_reads;
 }
 
-// Reset the per-pass device counters; out_n restarts at `out_start`.
-int reset_misc(kmer_analysis* h, unsigned long long out_start) {
+// Reset the per-pass device counters; out_n restarts at `out_start` and the
+// scatter's emitted-window count at `emitted` (kept when only later stages re-run).
+int reset_misc(kmer_analysis* h, unsigned long long out_start, unsigned long long emitted = 0) {
     Misc m{};
     m.out_n = out_start;
+    m.stats[2] = emitted;
     std::memcpy(h->host_misc, &m, sizeof m);
     CK(cudaMemcpyAsync(h->misc.p, h->host_misc, sizeof(Misc), cudaMemcpyHostToDevice, h->stream));
     return KMER_OK;
@@ -511,7 +519,11 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         CK(cudaMemsetAsync(h->l1_fill.p, 0, P1 * 8, h->stream));
         unsigned long long l2_capacity = 0;
         if (g.p2) {
-            l2_capacity = exact_leaf.empty() ? l1_total + l1_total / 4 + 66ull * P + 1024 : exact_leaf[P];
+            // sum over buckets of P2 leaves of (mean * slack / 256 + 256) records, mean <= n_b / P2 + 1
+            l2_capacity = exact_leaf.empty()
+                              ? (unsigned long long)(((double)h->l2_slack_num / 256.0) * (double)(l1_total + P)) +
+                                    257ull * P + 1024
+                              : exact_leaf[P];
             TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
             TRY(h->l2_base.ensure(P1 * 8));
             TRY(h->l2_leafcap.ensure(P1 * 4));
@@ -587,7 +599,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
                 j.l2_rec = h->l2_rec.as<unsigned long long>();
                 j.l2_leaf_start = h->l2_leaf_start.as<unsigned long long>();
                 h->st.retries++;
-                TRY(reset_misc(h, out_start));
+                TRY(reset_misc(h, out_start, m.stats[2]));
                 continue;
             }
             if (m.status & (ST_OUT_OVERFLOW | ST_FALLBACK_FULL)) {
@@ -598,7 +610,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
                 }
                 fill_job_outputs(h, j);
                 h->st.retries++;
-                TRY(reset_misc(h, out_start));
+                TRY(reset_misc(h, out_start, m.stats[2]));
                 continue;
             }
             TRY(status_error(m.status));
@@ -606,6 +618,9 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             TRY(run_fallbacks(h, j, m.fb_n));
             const Misc fin = *h->host_misc;
             if (fin.status & ST_OUT_OVERFLOW) return fail(KMER_ERR_CUDA, "fallback output overflow");
+            if (fin.stats[0] != fin.stats[2])  // every emitted window must be counted by exactly one leaf
+                return fail(KMER_ERR_CUDA, "internal: %llu windows emitted but %llu counted", fin.stats[2],
+                            fin.stats[0]);
             h->n_out = fin.out_n;
             h->res_windows += fin.stats[0];
             h->res_distinct += fin.stats[1];

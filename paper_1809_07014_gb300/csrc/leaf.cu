@@ -6,18 +6,20 @@
 // arrays.
 //
 // Persistent CTAs walk the leaves; while one leaf is being swept, the first
-// batch of the next leaf's records is already loading into registers.  The
-// sweep is per warp: a warp ballots over its slice of the table, lists its
-// survivors in shared memory, reserves their output rows with one atomic and
-// then writes them with every lane busy (no block barrier in the sweep).
+// batch of the next leaf's records is already loading into registers.
 //
-// Table slot (SoA, stride = table capacity): tail word (0 = empty; record
-// tail with the extension bits replaced by a mark bit; bit 0 = being
-// published), W-1 head words, a 32-bit count and eight 16-bit extension
-// tallies.  A 16-bit tally can only wrap if its k-mer's count reaches 65536;
-// the thread that takes a count to 65536 flags the leaf, and flagged leaves
-// (and leaves whose distinct keys do not fit) are recounted exactly by the
-// HBM-table fallback.
+// Table (shared memory, planes of `cap_max` entries, a leaf uses the first
+// `cap` slots): the tail word of each slot (0 = empty; record tail with the
+// extension bits replaced by a mark bit; bit 0 = being published, W > 1
+// only), W-1 head words, and nine 16-bit tallies packed in five 32-bit planes:
+// left A, C, G, T, "no left extension" (so that count = sum of the five left
+// lanes and needs no counter of its own), right A, C, G, T.  Slots are probed
+// in groups of four (one 32-byte read compares four keys).  A leaf with
+// 65536 records or more (where a 16-bit tally could wrap), or whose keys do
+// not fit, is recounted exactly by the HBM-table fallback.
+//
+// Every plane is zero between leaves: the sweep clears each slot after
+// reading it, so no separate clearing pass is needed.
 #include "kernels.h"
 #include "roll.cuh"
 
@@ -25,8 +27,10 @@ namespace kmer {
 
 constexpr int kLeafThreads = 512;
 constexpr int kLeafWarps = kLeafThreads / 32;
-constexpr unsigned kLeafFull = 1u, kLeafHeavy = 2u, kLeafTimeout = 4u;
+constexpr unsigned kLeafFull = 1u, kLeafTimeout = 4u;
 constexpr unsigned kSpinLimit = 1u << 22;
+constexpr unsigned kMaxGroupProbes = 16;  // 64 slots; a longer chain sends the leaf to the fallback
+constexpr unsigned kLanePlanes = 5;
 
 template <int W>
 struct LeafShape {
@@ -34,7 +38,8 @@ struct LeafShape {
     static constexpr int B = U * kLeafThreads;
 };
 
-__host__ __device__ inline size_t leaf_slot_bytes(unsigned W) { return (size_t)8 * W + 4 + 16 + 4; }
+// bytes per slot: tail, heads, 5 tally planes, survivor list entry
+__host__ __device__ inline size_t leaf_slot_bytes(unsigned W) { return (size_t)8 * W + 4 * kLanePlanes + 4; }
 
 size_t leaf_smem_bytes(unsigned W, unsigned cap) { return leaf_slot_bytes(W) * cap + 64; }
 
@@ -90,64 +95,87 @@ __device__ __forceinline__ void load_batch(const LeafInfo& li, unsigned long lon
     }
 }
 
+struct Table {
+    unsigned long long* tail;   // [cap_max]
+    unsigned long long* heads;  // [(W-1) * cap_max]
+    unsigned* lanes;            // [5 * cap_max]
+    unsigned* list;             // [cap_max]
+    unsigned stride;            // cap_max
+};
+
+// Two adjacent slots' tail words, re-read from shared memory on every call.
+__device__ __forceinline__ ulonglong2 lds_v2_volatile(const unsigned long long* p) {
+    ulonglong2 r;
+    asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(r.x), "=l"(r.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return r;
+}
+
+// Lane q in 0..8 lives in plane q >> 1, half q & 1.
+__device__ __forceinline__ void bump(const Table& t, unsigned slot, unsigned q) {
+    atomicAdd(&t.lanes[(q >> 1) * t.stride + slot], 1u << (16 * (q & 1)));
+}
+
 template <int W>
-__device__ __forceinline__ void insert_record(const unsigned long long (&rec)[W], unsigned cap, unsigned limit,
-                                              unsigned long long* ttail, unsigned long long* heads, unsigned* cnt,
-                                              unsigned* ext, unsigned* s_claimed, unsigned* s_flags) {
+__device__ __forceinline__ void insert_record(const Table& t, const unsigned long long (&rec)[W], unsigned ngroups,
+                                              unsigned* s_flags) {
     const unsigned long long tail = rec[W - 1];
     const unsigned e5 = (unsigned)(tail & 31ull);
     const unsigned long long ktail = (tail & ~63ull) | kKeyMark;
     const unsigned long long zl = tail >> 6;
-    unsigned slot = (unsigned)(((unsigned long long)(unsigned)(zl ^ (zl >> 32)) * cap) >> 32);
+    unsigned g = (unsigned)(((unsigned long long)(unsigned)(zl ^ (zl >> 32)) * ngroups) >> 32);
     int found = -1;
-    for (unsigned probe = 0; probe < cap; ++probe) {
-        unsigned long long cur = *(volatile unsigned long long*)&ttail[slot];
-        if (cur == 0ull) {
-            const unsigned long long prev = atomicCAS(&ttail[slot], 0ull, ktail | kBusy);
-            if (prev == 0ull) {
-                cnt[slot] = 0;
-                *reinterpret_cast<uint4*>(&ext[slot * 4]) = make_uint4(0, 0, 0, 0);
+    for (unsigned probe = 0; probe < kMaxGroupProbes && found < 0; ++probe) {
+        unsigned long long* grp = t.tail + 4 * g;
+        const ulonglong2 a = lds_v2_volatile(grp);
+        const ulonglong2 b = lds_v2_volatile(grp + 2);
+        unsigned long long cur[4] = {a.x, a.y, b.x, b.y};
+        for (int s = 0; s < 4 && found < 0; ++s) {
+            unsigned long long c = cur[s];
+            if (c == 0ull) {  // first empty slot of the group: try to claim it
+                const unsigned long long prev = atomicCAS(&grp[s], 0ull, W == 1 ? ktail : (ktail | kBusy));
+                if (prev == 0ull) {
+                    if (W > 1) {
 #pragma unroll
-                for (int w = 0; w < W - 1; ++w) heads[(size_t)w * cap + slot] = rec[w];
-                __threadfence_block();
-                atomicExch(&ttail[slot], ktail);
-                if (atomicAdd(s_claimed, 1u) + 1 >= limit) atomicOr(s_flags, kLeafFull);
-                found = (int)slot;
+                        for (int w = 0; w < W - 1; ++w) t.heads[(size_t)w * t.stride + 4 * g + s] = rec[w];
+                        __threadfence_block();
+                        atomicExch(&grp[s], ktail);
+                    }
+                    found = (int)(4 * g + s);
+                    break;
+                }
+                c = prev;
+            }
+            if ((c & ~kBusy) != ktail) continue;
+            if (W == 1) {
+                found = (int)(4 * g + s);
                 break;
             }
-            cur = prev;
-        }
-        if ((cur & ~kBusy) == ktail) {
             unsigned spins = 0;
-            while (cur & kBusy) {
-                if (++spins > kSpinLimit) break;
-                cur = *(volatile unsigned long long*)&ttail[slot];
-            }
-            if (cur & kBusy) {
-                atomicOr(s_flags, kLeafTimeout);
-                return;
+            while (c & kBusy) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(s_flags, kLeafTimeout);
+                    return;
+                }
+                c = *(volatile unsigned long long*)&grp[s];
             }
             __threadfence_block();
             bool same = true;
 #pragma unroll
             for (int w = 0; w < W - 1; ++w)
-                same = same && (*(volatile unsigned long long*)&heads[(size_t)w * cap + slot] == rec[w]);
-            if (same) {
-                found = (int)slot;
-                break;
-            }
+                same = same && (*(volatile unsigned long long*)&t.heads[(size_t)w * t.stride + 4 * g + s] == rec[w]);
+            if (same) found = (int)(4 * g + s);
         }
-        slot = slot + 1 == cap ? 0 : slot + 1;
+        g = g + 1 == ngroups ? 0 : g + 1;
     }
     if (found < 0) {
         atomicOr(s_flags, kLeafFull);
         return;
     }
-    const unsigned c = atomicAdd(&cnt[found], 1u);
-    if (c == 65535u) atomicOr(s_flags, kLeafHeavy);
     const unsigned l = e5 / 5u, r = e5 - 5u * l;
-    if (l) atomicAdd(&ext[found * 4 + ((l - 1) >> 1)], 1u << (16 * ((l - 1) & 1)));
-    if (r) atomicAdd(&ext[found * 4 + 2 + ((r - 1) >> 1)], 1u << (16 * ((r - 1) & 1)));
+    bump(t, (unsigned)found, l ? l - 1 : 4u);  // every window has exactly one left lane
+    if (r) bump(t, (unsigned)found, 4u + r);
 }
 
 template <int W>
@@ -155,118 +183,152 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job j, cons
                                                               const unsigned n_leaves) {
     constexpr int U = LeafShape<W>::U, B = LeafShape<W>::B;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_claimed, s_flags;
+    __shared__ unsigned s_flags;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-    unsigned leaf = blockIdx.x;
-    if (leaf >= n_leaves) return;
-    LeafInfo li = leaf_info(j, leaf);
-    unsigned long long batch[U][W];
-    load_batch<W>(li, 0, batch);
-
-    for (;;) {
-        // ---------------------------------------------------------- count
-        if (li.ok) {
-            const unsigned long long n = li.n;
-            const unsigned long long want = ((n * j.table_ratio_num) >> 16) + 512;
-            const unsigned cap = (unsigned)(want < cap_max ? ((want + 511) & ~511ull) : cap_max);
-            unsigned long long* ttail = reinterpret_cast<unsigned long long*>(smem);
-            unsigned long long* heads = ttail + cap;
-            unsigned* cnt = reinterpret_cast<unsigned*>(heads + (size_t)(W - 1) * cap);
-            unsigned* ext = cnt + cap;
-            unsigned* list = ext + 4 * (size_t)cap;
-            for (unsigned s = threadIdx.x; s < cap; s += kLeafThreads) ttail[s] = 0ull;
-            if (threadIdx.x == 0) { s_claimed = 0; s_flags = 0; }
-            __syncthreads();
-            const unsigned limit = cap - cap / 8;  // keep probe chains short; fuller leaves go to the fallback
-            for (unsigned long long first = 0; first < n; first += B) {
-                if (first) load_batch<W>(li, first, batch);
+    Table t;
+    t.stride = cap_max;
+    t.tail = reinterpret_cast<unsigned long long*>(smem);
+    t.heads = t.tail + cap_max;
+    t.lanes = reinterpret_cast<unsigned*>(t.heads + (size_t)(W - 1) * cap_max);
+    t.list = t.lanes + (size_t)kLanePlanes * cap_max;
+    for (unsigned s = threadIdx.x; s < cap_max; s += kLeafThreads) {
+        t.tail[s] = 0ull;
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const unsigned long long i = first + (unsigned long long)u * kLeafThreads + threadIdx.x;
-                    if (i < n && !*(volatile unsigned*)&s_flags)
-                        insert_record<W>(batch[u], cap, limit, ttail, heads, cnt, ext, &s_claimed, &s_flags);
-                }
+        for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+    }
+    if (threadIdx.x == 0) s_flags = 0;
+
+    unsigned long long windows = 0, distinct = 0;  // this thread's share, added once at the end
+    unsigned leaf = blockIdx.x;
+    LeafInfo li;
+    li.ok = false;
+    unsigned long long batch[U][W];
+    if (leaf < n_leaves) {
+        li = leaf_info(j, leaf);
+        load_batch<W>(li, 0, batch);
+    }
+    __syncthreads();
+
+    while (leaf < n_leaves) {
+        const unsigned next = leaf + gridDim.x;
+        if (!li.ok || li.n >= 65536ull) {
+            if (li.ok && threadIdx.x == 0) {  // 16-bit tallies could wrap: exact recount in HBM
+                const unsigned idx = atomicAdd(j.fb_n, 1u);
+                if (idx < j.fb_cap) j.fb_list[idx] = leaf; else set_status(j, ST_FALLBACK_FULL);
             }
-            __syncthreads();
-            const unsigned flags = s_flags;
-            const unsigned claimed = s_claimed;
-            // the next leaf's first batch loads while this one is swept
-            const unsigned next = leaf + gridDim.x;
-            LeafInfo nli;
-            nli.ok = false;
-            if (next < n_leaves) {
-                nli = leaf_info(j, next);
-                load_batch<W>(nli, 0, batch);
+            leaf = next;
+            if (leaf < n_leaves) {
+                li = leaf_info(j, leaf);
+                load_batch<W>(li, 0, batch);
             }
-            if (flags & kLeafTimeout) {
-                if (threadIdx.x == 0) set_status(j, ST_TIMEOUT);
-            } else if (flags) {  // table too full or a tally may have wrapped: exact recount in HBM
-                if (threadIdx.x == 0) {
+            continue;
+        }
+        // ---------------------------------------------------------- count
+        const unsigned long long n = li.n;
+        const unsigned long long want = ((n * j.table_ratio_num) >> 16) + 512;
+        const unsigned cap = (unsigned)(want < cap_max ? ((want + 511) & ~511ull) : cap_max);
+        const unsigned ngroups = cap / 4;
+        for (unsigned long long first = 0; first < n; first += B) {
+            if (first) load_batch<W>(li, first, batch);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned long long i = first + (unsigned long long)u * kLeafThreads + threadIdx.x;
+                if (i < n && !*(volatile unsigned*)&s_flags) insert_record<W>(t, batch[u], ngroups, &s_flags);
+            }
+        }
+        __syncthreads();
+        const unsigned flags = s_flags;
+        // the next leaf's first batch loads while this one is swept
+        LeafInfo nli;
+        nli.ok = false;
+        if (next < n_leaves) {
+            nli = leaf_info(j, next);
+            load_batch<W>(nli, 0, batch);
+        }
+        const unsigned per = cap / kLeafWarps;  // a multiple of 32
+        const unsigned s0 = wid * per;
+        if (flags) {
+            if (threadIdx.x == 0) {
+                if (flags & kLeafTimeout) {
+                    set_status(j, ST_TIMEOUT);
+                } else {  // keys did not fit: exact recount in HBM
                     const unsigned idx = atomicAdd(j.fb_n, 1u);
                     if (idx < j.fb_cap) j.fb_list[idx] = leaf; else set_status(j, ST_FALLBACK_FULL);
                 }
-            } else {
-                if (threadIdx.x == 0) {
-                    atomicAdd(j.stats + 0, n);
-                    atomicAdd(j.stats + 1, (unsigned long long)claimed);
-                }
-                // ------------------------------------------------------ sweep (per warp)
-                const unsigned per = cap / kLeafWarps;  // a multiple of 32
-                const unsigned s0 = wid * per;
-                unsigned* mylist = list + s0;
-                unsigned count = 0;
-                for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
-                    const unsigned long long tl = ttail[s];
-                    const bool ok = tl != 0ull && cnt[s] >= j.min_count;
-                    const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (ok) mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
-                    count += __popc(m);
-                }
-                __syncwarp();
-                unsigned long long wbase = 0;
-                if (lane == 0 && count) wbase = atomicAdd(j.out_n, (unsigned long long)count);
-                wbase = __shfl_sync(0xffffffffu, wbase, 0);
-                for (unsigned i = lane; i < count; i += 32) {
-                    const unsigned s = mylist[i];
-                    const unsigned long long pos = wbase + i;
-                    if (pos >= j.out_cap) {
-                        set_status(j, ST_OUT_OVERFLOW);
-                        continue;
-                    }
-                    const unsigned long long tl = ttail[s];
-                    const unsigned c = cnt[s];
-                    unsigned long long key[W];
-#pragma unroll
-                    for (int w = 0; w < W - 1; ++w) key[w] = heads[(size_t)w * cap + s];
-                    const unsigned long long z = record_z(j.g, j.pass, li.bucket, tl);
-                    key[W - 1] = z_to_tail<W>(z, key, j.g.bt);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) j.out_keys[pos * W + w] = key[w];
-                    j.out_count[pos] = c;
-                    const uint4 e = *reinterpret_cast<const uint4*>(&ext[s * 4]);
-                    unsigned nl[4] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16};
-                    unsigned nr[4] = {e.z & 0xFFFFu, e.z >> 16, e.w & 0xFFFFu, e.w >> 16};
-                    uint4* eo = reinterpret_cast<uint4*>(j.out_ext + pos * 8);
-                    eo[0] = make_uint4(nl[0], nl[1], nl[2], nl[3]);
-                    eo[1] = make_uint4(nr[0], nr[1], nr[2], nr[3]);
-                    reinterpret_cast<uchar2*>(j.out_cls)[pos] =
-                        make_uchar2(classify_side(nl, c, j), classify_side(nr, c, j));
-                }
             }
-            __syncthreads();  // the table is reused by the next leaf
-            leaf = next;
-            li = nli;
+            for (unsigned s = s0 + lane; s < s0 + per; s += 32) {  // leave the table clean
+                t.tail[s] = 0ull;
+#pragma unroll
+                for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+            }
         } else {
-            const unsigned next = leaf + gridDim.x;
-            if (next >= n_leaves) break;
-            leaf = next;
-            li = leaf_info(j, leaf);
-            load_batch<W>(li, 0, batch);
-            continue;
+            if (threadIdx.x == 0) windows += n;
+            // ------------------------------------------------------ sweep (per warp)
+            unsigned* mylist = t.list + s0;
+            unsigned count = 0;
+            for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
+                const unsigned long long tl = t.tail[s];
+                const unsigned p0 = t.lanes[s], p1 = t.lanes[cap_max + s], p2 = t.lanes[2 * cap_max + s];
+                const unsigned c = (p0 & 0xFFFFu) + (p0 >> 16) + (p1 & 0xFFFFu) + (p1 >> 16) + (p2 & 0xFFFFu);
+                const bool ok = tl != 0ull && c >= j.min_count;
+                distinct += tl != 0ull ? 1 : 0;
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
+                } else {
+                    t.tail[s] = 0ull;
+#pragma unroll
+                    for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+                }
+                count += __popc(m);
+            }
+            __syncwarp();
+            unsigned long long wbase = 0;
+            if (lane == 0 && count) wbase = atomicAdd(j.out_n, (unsigned long long)count);
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            for (unsigned i = lane; i < count; i += 32) {
+                const unsigned s = mylist[i];
+                const unsigned long long pos = wbase + i;
+                const unsigned long long tl = t.tail[s];
+                unsigned pl[kLanePlanes];
+#pragma unroll
+                for (unsigned p = 0; p < kLanePlanes; ++p) pl[p] = t.lanes[p * cap_max + s];
+                unsigned long long key[W];
+#pragma unroll
+                for (int w = 0; w < W - 1; ++w) key[w] = t.heads[(size_t)w * cap_max + s];
+                t.tail[s] = 0ull;
+#pragma unroll
+                for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+                if (pos >= j.out_cap) {
+                    set_status(j, ST_OUT_OVERFLOW);
+                    continue;
+                }
+                const unsigned nl[4] = {pl[0] & 0xFFFFu, pl[0] >> 16, pl[1] & 0xFFFFu, pl[1] >> 16};
+                const unsigned nr[4] = {pl[2] >> 16, pl[3] & 0xFFFFu, pl[3] >> 16, pl[4] & 0xFFFFu};
+                const unsigned c = nl[0] + nl[1] + nl[2] + nl[3] + (pl[2] & 0xFFFFu);
+                const unsigned long long z = record_z(j.g, j.pass, li.bucket, tl);
+                key[W - 1] = z_to_tail<W>(z, key, j.g.bt);
+#pragma unroll
+                for (int w = 0; w < W; ++w) j.out_keys[pos * W + w] = key[w];
+                j.out_count[pos] = c;
+                uint4* eo = reinterpret_cast<uint4*>(j.out_ext + pos * 8);
+                eo[0] = make_uint4(nl[0], nl[1], nl[2], nl[3]);
+                eo[1] = make_uint4(nr[0], nr[1], nr[2], nr[3]);
+                reinterpret_cast<uchar2*>(j.out_cls)[pos] =
+                    make_uchar2(classify_side(nl, c, j), classify_side(nr, c, j));
+            }
         }
-        if (leaf >= n_leaves) break;
+        if (threadIdx.x == 0) s_flags = 0;
+        __syncthreads();  // the clean table is reused by the next leaf
+        leaf = next;
+        li = nli;
     }
+    // per-thread shares of the statistics
+#pragma unroll
+    for (int o = 16; o; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
+    if (lane == 0 && distinct) atomicAdd(j.stats + 1, distinct);
+    if (threadIdx.x == 0 && windows) atomicAdd(j.stats + 0, windows);
 }
 
 template <int W>

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kStageThreads) l2_plan_kernel(const Job j, uns
     }
     if (threadIdx.x == 0) {
         j.tile_prefix[P1] = s_tiles;
-        if (s_slots > l2_capacity) atomicOr(j.status, ST_L2_OVERFLOW);
+        if (s_slots > l2_capacity) atomicOr(j.status, ST_L2_OVERFLOW | ST_L2_PLAN);
     }
 }
 
@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job j) {
     __syncthreads();
     const unsigned zb = j.g.zl_bits();
     // the planner found the leaf layout larger than the buffer: write nothing, the host retries
-    if (*(volatile unsigned*)j.status & ST_L2_OVERFLOW) return;
+    // (only the planner's bit: leaf overflows found by other CTAs must not stop the
+    // counting, the host needs complete per-leaf totals for the exact layout)
+    if (*(volatile unsigned*)j.status & ST_L2_PLAN) return;
     const unsigned long long total = j.tile_prefix[P1];
     for (unsigned long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
         // bucket of this tile: last b with tile_prefix[b] <= tile
