@@ -146,7 +146,7 @@ void kmer_analysis_default_params(kmer_analysis_params *p, uint32_t k);
 /* Packs reads for the device (step a1).  Reads are given flat: read i is
  * bases[offsets[i] .. offsets[i+1]) with one quality byte per base in quals
  * (same indexing); offsets has n_reads + 1 non-decreasing entries, offsets[0]
- * is normally 0, and every read is shorter than 2^32 bases.  `where` says
+ * is normally 0, and every read is shorter than 2^31 bases.  `where` says
  * whether bases, quals and offsets are host (KMER_HOST, any host memory;
  * pinned memory copies fastest) or device (KMER_DEVICE) pointers.  The
  * quality test (Phred >= qual_threshold, Phred = byte - qual_offset) is
@@ -155,7 +155,7 @@ void kmer_analysis_default_params(kmer_analysis_params *p, uint32_t k);
  * released once this call returns (it synchronises the stream).  The readset
  * owns its packed copy (about 0.5 byte per base plus 16 bytes per read).
  * Errors: INVALID_ARG (null pointer with n_reads > 0, decreasing offsets,
- * a read of 2^32 bases or more), OOM, CUDA. */
+ * a read of 2^31 bases or more), OOM, CUDA. */
 int kmer_readset_create(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
                         uint32_t qual_offset, uint32_t qual_threshold, int where, void *cuda_stream,
                         kmer_readset_t **out);

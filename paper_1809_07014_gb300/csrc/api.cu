@@ -186,8 +186,8 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
         for (uint64_t i = 0; i < n_reads; ++i) {
             if (offsets[i + 1] < offsets[i])
                 return fail(KMER_ERR_INVALID_ARG, "offsets decrease at read %llu", (unsigned long long)i);
-            if (offsets[i + 1] - offsets[i] > 0xFFFFFFFFull)
-                return fail(KMER_ERR_INVALID_ARG, "read %llu is 2^32 bases or longer", (unsigned long long)i);
+            if (offsets[i + 1] - offsets[i] >= 0x80000000ull)
+                return fail(KMER_ERR_INVALID_ARG, "read %llu is 2^31 bases or longer", (unsigned long long)i);
         }
         const unsigned long long nb = offsets[n_reads];
         TRY(rs->tmp_bases.ensure(nb + 16));
@@ -223,7 +223,7 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
     CK(cudaStreamSynchronize(s));
     const unsigned bad_flags = (unsigned)(host[kLenHist] & 0xFFFFFFFFull);
     if (bad_flags & 1u) return fail(KMER_ERR_INVALID_ARG, "offsets are not non-decreasing");
-    if (bad_flags & 2u) return fail(KMER_ERR_INVALID_ARG, "a read is 2^32 bases or longer");
+    if (bad_flags & 2u) return fail(KMER_ERR_INVALID_ARG, "a read is 2^31 bases or longer");
     const unsigned long long total_blocks = host[kLenHist + 2];
     TRY(rs->blocks.ensure(std::max<unsigned long long>(total_blocks, 1) * sizeof(PackedBlock)));
     int num_sms = 0;

@@ -121,7 +121,7 @@ __global__ void read_geometry_kernel(const unsigned long long* offsets, unsigned
             atomicAdd(&hist[kLenExact], 1ull);
             atomicAdd(&hist[kLenExact + 1], L);
         }
-        if (L > 0xFFFFFFFFull) atomicOr(bad, 2u);
+        if (L >= 0x80000000ull) atomicOr(bad, 2u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kLenHist; i += blockDim.x)

@@ -76,7 +76,7 @@ struct L2Dest {
     }
 };
 
-template <int W>
+template <int W, unsigned MAXPER>
 __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job j) {
     constexpr unsigned S = RepartShape<W>::S;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job j) {
             b.meta[e] = m;
         }
         L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[bucket], j.l2_leafcap[bucket], bucket << j.g.p2};
-        flush_stage<W>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
+        flush_stage<W, MAXPER>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
     }
 }
 
@@ -140,13 +140,20 @@ cudaError_t launch_l2_plan(const Job& j, unsigned long long l2_capacity, cudaStr
     return cudaGetLastError();
 }
 
+template <int W, unsigned MAXPER>
+static cudaError_t launch_repart_wp(const Job& j, int num_sms, cudaStream_t s) {
+    const size_t smem = repart_smem_bytes(W, j.g.p2);
+    cudaError_t e =
+        cudaFuncSetAttribute(repart_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(j);
+    return cudaGetLastError();
+}
+
 template <int W>
 static cudaError_t launch_repart_w(const Job& j, int num_sms, cudaStream_t s) {
-    const size_t smem = repart_smem_bytes(W, j.g.p2);
-    cudaError_t e = cudaFuncSetAttribute(repart_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    repart_kernel<W><<<num_sms * 2, kStageThreads, smem, s>>>(j);
-    return cudaGetLastError();
+    if ((1u << j.g.p2) <= 2 * kStageThreads) return launch_repart_wp<W, 2>(j, num_sms, s);
+    return launch_repart_wp<W, kMaxStageDest / kStageThreads>(j, num_sms, s);
 }
 
 cudaError_t launch_repart(const Job& j, int num_sms, cudaStream_t s) {

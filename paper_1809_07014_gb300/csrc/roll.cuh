@@ -101,6 +101,74 @@ struct Roll {
     }
 };
 
+// k <= 31: the whole k-mer fits one word; positions and the quality history
+// fit 32 bits (reads are shorter than 2^31 bases).
+template <>
+struct Roll<1> {
+    unsigned long long fwd, rc, mask, cur;
+    unsigned curn, curg, gh, out, L, k, sh;
+    int last_n;
+    uint4 nxt;
+    const PackedBlock* blk;
+
+    __device__ void init(const Job& j, unsigned long long r) {
+        const unsigned long long a = j.offsets[r];
+        L = (unsigned)(j.offsets[r + 1] - a);
+        blk = j.blocks + j.blk_off[r];
+        k = j.g.k;
+        sh = 2 * k - 2;
+        mask = low_mask(2 * k);
+        fwd = rc = cur = 0;
+        curn = curg = gh = out = 0;
+        last_n = -1;
+        nxt = L ? __ldg(reinterpret_cast<const uint4*>(blk)) : make_uint4(0, 0, 0, 0);
+    }
+
+    __device__ __forceinline__ bool step(unsigned long long t64, unsigned long long (&key)[1], unsigned& lcode,
+                                         unsigned& rcode) {
+        const unsigned t = (unsigned)t64;
+        const bool in = t < L;
+        unsigned b = 0, good = 0, isn = 0;
+        if (in) {
+            if ((t & 31) == 0) {
+                cur = ((unsigned long long)nxt.y << 32) | nxt.x;
+                curn = nxt.z;
+                curg = nxt.w;
+                if (t + 32 < L) nxt = __ldg(reinterpret_cast<const uint4*>(blk + (t >> 5) + 1));
+            }
+            b = (unsigned)(cur >> 62);
+            cur <<= 2;
+            isn = curn & 1u;
+            curn >>= 1;
+            good = curg & 1u;
+            curg >>= 1;
+        }
+        bool emit = false;
+        if (t >= k && last_n < (int)(t - k)) {
+            emit = true;
+            unsigned lc = (t > k && ((gh >> k) & 1u)) ? out + 1 : 0;
+            unsigned rcd = (in && good) ? b + 1 : 0;
+            const bool flip = rc < fwd;
+            key[0] = flip ? rc : fwd;
+            if (flip) {  // the key reads the other strand: swap sides, complement bases
+                const unsigned nl = rcd ? 5 - rcd : 0, nr = lc ? 5 - lc : 0;
+                lc = nl;
+                rcd = nr;
+            }
+            lcode = lc;
+            rcode = rcd;
+        }
+        if (in) {
+            out = (unsigned)(fwd >> sh) & 3u;
+            fwd = ((fwd << 2) | b) & mask;
+            rc = (rc >> 2) | ((unsigned long long)(3u - b) << sh);
+            gh = (gh << 1) | good;
+            if (isn) last_n = (int)t;
+        }
+        return emit;
+    }
+};
+
 // Record of one window (words 0..W-2 = head words, word W-1 = tail) and its
 // level-1 bucket; returns false when the window belongs to another pass.
 template <int W>

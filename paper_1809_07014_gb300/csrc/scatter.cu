@@ -24,8 +24,9 @@ struct L1Dest {
     __device__ unsigned long long cap(unsigned d) const { return __ldg(capp + d); }
 };
 
-template <int W>
-__global__ void __launch_bounds__(kStageThreads, 2)
+// MAXPER: destinations handled by one thread in a flush (fan-out / 256).
+template <int W, unsigned MAXPER>
+__global__ void __launch_bounds__(kStageThreads, W == 1 ? 3 : 2)
 scatter_kernel(const Job j, const unsigned long long r0, const unsigned long long r1) {
     constexpr unsigned R = ScatterShape<W>::R, S = ScatterShape<W>::S;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -69,7 +70,7 @@ scatter_kernel(const Job j, const unsigned long long r0, const unsigned long lon
             }
             b.meta[e] = m;
         }
-        flush_stage<W>(b, S, P, dest, j.l1_rec, j.status, ST_L1_OVERFLOW);
+        flush_stage<W, MAXPER>(b, S, P, dest, j.l1_rec, j.status, ST_L1_OVERFLOW);
     }
     // windows emitted into this pass (a check against the leaves' totals)
 #pragma unroll
@@ -87,17 +88,24 @@ size_t scatter_smem_bytes(unsigned W, unsigned p1) {
     }
 }
 
-template <int W>
-static cudaError_t launch_scatter_w(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
+template <int W, unsigned MAXPER>
+static cudaError_t launch_scatter_wp(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
     const size_t smem = scatter_smem_bytes(W, j.g.p1);
-    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(scatter_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned long long n = r1 - r0;
     const unsigned long long grid = (n + kStageThreads - 1) / kStageThreads;
     if (grid == 0) return cudaSuccess;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    scatter_kernel<W><<<(unsigned)grid, kStageThreads, smem, s>>>(j, r0, r1);
+    scatter_kernel<W, MAXPER><<<(unsigned)grid, kStageThreads, smem, s>>>(j, r0, r1);
     return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_scatter_w(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
+    if ((1u << j.g.p1) <= 2 * kStageThreads) return launch_scatter_wp<W, 2>(j, r0, r1, s);
+    return launch_scatter_wp<W, kMaxStageDest / kStageThreads>(j, r0, r1, s);
 }
 
 cudaError_t launch_scatter(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {

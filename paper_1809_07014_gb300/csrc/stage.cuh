@@ -103,7 +103,7 @@ __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigne
 // slot 0 of d, cap(d) -> slots of d.  Records past cap are dropped and
 // reported through `status` (the host then retries with exact capacities).
 // hist is left zeroed for the next round.
-template <int W, class Dest>
+template <int W, unsigned MAXPER, class Dest>
 __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
                             unsigned* status, unsigned overflow_bit) {
     __syncthreads();
@@ -117,9 +117,8 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     unsigned run = block_scan_u32(mine, b.warp_tmp, &total);
     // reservations of this thread's destinations are independent: unrolled so
     // that all of them are in flight together
-    constexpr unsigned kMaxPer = kMaxStageDest / kStageThreads;
 #pragma unroll
-    for (unsigned i = 0; i < kMaxPer; ++i) {
+    for (unsigned i = 0; i < MAXPER; ++i) {
         const unsigned d = d0 + i;
         if (i < per && d < P) {
             const unsigned h = b.hist[d];
