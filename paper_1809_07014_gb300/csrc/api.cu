@@ -124,6 +124,7 @@ struct kmer_analysis {
     DevBuf l2_rec, l2_base, l2_leafcap, l2_fill, l2_leaf_start, tile_prefix;
     DevBuf out_keys, out_count, out_ext, out_cls;
     DevBuf fb_list, hbm, misc;
+    DevBuf d_ajob, d_sjobs, d_tile_off, d_leaf_off, d_job_tile_off;  // job descriptors and work maps
     unsigned long long out_cap = 0, fb_cap = 0;
     Misc* host_misc = nullptr;  // pinned
     // profiling (KMER_FLAG_PROFILE): one begin/end event pair per stage
@@ -145,7 +146,8 @@ struct kmer_analysis {
     size_t device_bytes() const {
         const DevBuf* bs[] = {&l1_rec, &l1_start, &l1_cap, &l1_fill, &l2_rec, &l2_base, &l2_leafcap, &l2_fill,
                               &l2_leaf_start, &tile_prefix, &out_keys, &out_count, &out_ext, &out_cls,
-                              &fb_list, &hbm, &misc};
+                              &fb_list, &hbm, &misc, &d_ajob, &d_sjobs, &d_tile_off, &d_leaf_off,
+                              &d_job_tile_off};
         size_t t = 0;
         for (auto* b : bs) t += b->bytes;
         return t;
@@ -403,6 +405,15 @@ void set_readset(Job& j, const kmer_readset* rs) {
     j.n_reads = rs->n_reads;
 }
 
+// Copy a host array to a device buffer (pageable source: the call returns once
+// the data is staged, so the host array may change right after).
+template <class T>
+int upload(kmer_analysis* h, DevBuf& dst, const std::vector<T>& src) {
+    TRY(dst.ensure(std::max<size_t>(src.size() * sizeof(T), 16)));
+    if (!src.empty()) CK(cudaMemcpyAsync(dst.p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return KMER_OK;
+}
+
 // Reset the per-pass device counters; out_n restarts at `out_start` and the
 // scatter's emitted-window count at `emitted` (kept when only later stages re-run).
 int reset_misc(kmer_analysis* h, unsigned long long out_start, unsigned long long emitted = 0) {
@@ -556,28 +567,46 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             j.l2_leaf_start = exact_leaf.empty() ? nullptr : h->l2_leaf_start.as<unsigned long long>();
         }
         fill_job_outputs(h, j);
-        TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
+        j.l2_capacity = exact_leaf.empty() ? l2_capacity : ~0ull;
+        // one scatter job per submitted readset, one CTA per 256 reads
+        std::vector<Job> sjobs;
+        std::vector<unsigned long long> tile_off(1, 0);
         for (const kmer_readset* rs : h->submitted) {
             if (rs->n_reads == 0) continue;
-            set_readset(j, rs);
-            CK(launch_scatter(j, 0, rs->n_reads, h->stream));
+            Job js = j;
+            set_readset(js, rs);
+            sjobs.push_back(js);
+            tile_off.push_back(tile_off.back() + (rs->n_reads + 255) / 256);
+        }
+        TRY(upload(h, h->d_sjobs, sjobs));
+        TRY(upload(h, h->d_tile_off, tile_off));
+        TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
+        if (!sjobs.empty()) {
+            CK(launch_scatter(W, h->d_sjobs.as<Job>(), h->d_tile_off.as<unsigned long long>(), (unsigned)sjobs.size(),
+                              tile_off.back(), g.p1, h->stream));
             h->st.launches++;
         }
         TRY(prof_end(h, kmer_analysis::STG_SCATTER));
+        const std::vector<unsigned long long> leaf_off = {0ull, (unsigned long long)P};
+        TRY(upload(h, h->d_leaf_off, leaf_off));
+        TRY(h->d_job_tile_off.ensure(2 * 8));
         // level 2 and leaves may be re-run without re-scattering
         for (unsigned sub_attempt = 0;; ++sub_attempt) {
             if (sub_attempt > 8) return fail(KMER_ERR_TABLE_FULL, "leaf buffers still too small after retries");
+            j.l2_capacity = exact_leaf.empty() ? l2_capacity : ~0ull;
+            TRY(upload(h, h->d_ajob, std::vector<Job>{j}));
             if (g.p2) {
                 CK(cudaMemsetAsync(h->l2_fill.p, 0, P * 8ull, h->stream));
                 TRY(prof_begin(h, kmer_analysis::STG_REPART));
-                // exact leaf layout: the uniform capacities computed by the planner are unused
-                CK(launch_l2_plan(j, exact_leaf.empty() ? l2_capacity : ~0ull, h->stream));
-                CK(launch_repart(j, h->num_sms, h->stream));
+                CK(launch_l2_plan(h->d_ajob.as<Job>(), 1, h->d_job_tile_off.as<unsigned long long>(), h->stream));
+                CK(launch_repart(W, h->d_ajob.as<Job>(), h->d_job_tile_off.as<unsigned long long>(), 1, g.p2,
+                                 h->num_sms, h->stream));
                 TRY(prof_end(h, kmer_analysis::STG_REPART));
-                h->st.launches += 2;
+                h->st.launches += 3;
             }
             TRY(prof_begin(h, kmer_analysis::STG_LEAF));
-            CK(launch_leaf(j, cap_max, h->num_sms, h->stream));
+            CK(launch_leaf(W, h->d_ajob.as<Job>(), h->d_leaf_off.as<unsigned long long>(), 1, P, cap_max, h->num_sms,
+                           h->stream));
             TRY(prof_end(h, kmer_analysis::STG_LEAF));
             h->st.launches++;
             TRY(read_misc(h));

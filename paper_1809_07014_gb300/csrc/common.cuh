@@ -154,6 +154,7 @@ struct Job {
     unsigned long long* l2_fill;           // per leaf: records offered
     const unsigned long long* l2_leaf_start;  // per leaf + 1: exact layout (after an overflow) or null
     unsigned long long* tile_prefix;       // per bucket + 1: level-2 tiles before it
+    unsigned long long l2_capacity;        // records the level-2 buffer holds (uniform layout check)
     // outputs (survivors)
     unsigned long long* out_keys;  // n * W
     unsigned int* out_count;
@@ -207,5 +208,16 @@ __device__ inline unsigned char classify_side(const unsigned (&n)[4], unsigned d
 }
 
 __device__ inline void set_status(const Job& j, unsigned bits) { atomicOr(j.status, bits); }
+
+// Index of the job that owns work unit `u`, given the exclusive prefix `off`
+// (n + 1 entries) of the jobs' unit counts (jobs with no units are skipped).
+__device__ __forceinline__ unsigned job_of(const unsigned long long* off, unsigned n, unsigned long long u) {
+    unsigned lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 }  // namespace kmer

@@ -19,20 +19,29 @@ cudaError_t launch_pack(const char* bases, const unsigned char* quals, const uns
                         const unsigned long long* blk_off, unsigned long long n, unsigned qual_offset,
                         unsigned qual_threshold, PackedBlock* out, int num_sms, cudaStream_t s);
 
-// Level-1 scatter (a2-a3 + partition): every window of reads [r0, r1) of the job.
+// All three stages take a device array of Job descriptors (all of key width
+// W) and work over every job of the array in one launch.
+
+// Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
+// tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles.
 size_t scatter_smem_bytes(unsigned W, unsigned p1);
-cudaError_t launch_scatter(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s);
+cudaError_t launch_scatter(unsigned W, const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                           unsigned long long tiles, unsigned max_p1, cudaStream_t s);
 
-// Per bucket: level-2 tile counts, leaf capacities and leaf region bases.
-cudaError_t launch_l2_plan(const Job& j, unsigned long long l2_capacity, cudaStream_t s);
-// Level-2 repartition of every level-1 bucket into its leaves.
+// Per analysis: level-2 tile counts, leaf capacities and leaf region bases;
+// then job_tile_off = prefix of the analyses' level-2 tiles (device array).
+cudaError_t launch_l2_plan(const Job* jobs, unsigned n_jobs, unsigned long long* job_tile_off, cudaStream_t s);
+// Level-2 repartition of every level-1 bucket of every analysis into its leaves.
 size_t repart_smem_bytes(unsigned W, unsigned p2);
-cudaError_t launch_repart(const Job& j, int num_sms, cudaStream_t s);
+cudaError_t launch_repart(unsigned W, const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
+                          unsigned max_p2, int num_sms, cudaStream_t s);
 
-// a4-a7 fused: count each leaf in shared memory, filter, classify, compact.
+// a4-a7 fused: count each leaf in shared memory, filter, classify, compact;
+// leaf_off = exclusive prefix (n_jobs + 1) of the analyses' leaf counts.
 unsigned leaf_table_cap(unsigned W, size_t smem_budget);
 size_t leaf_smem_bytes(unsigned W, unsigned cap);
-cudaError_t launch_leaf(const Job& j, unsigned cap_max, int num_sms, cudaStream_t s);
+cudaError_t launch_leaf(unsigned W, const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,
+                        unsigned long long leaves, unsigned cap_max, int num_sms, cudaStream_t s);
 
 // HBM open-addressing table (direct variant and fallback for leaves that do
 // not fit on chip).  Entries are zeroed by the caller (cudaMemsetAsync 0).

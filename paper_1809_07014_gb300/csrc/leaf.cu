@@ -178,13 +178,17 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
     if (r) bump(t, (unsigned)found, 4u + r);
 }
 
+// Persistent CTAs over the leaves of every analysis of key width W; `leaf_off`
+// is the exclusive prefix (n_jobs + 1) of the analyses' leaf counts.
 template <int W>
-__global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job j, const unsigned cap_max,
-                                                              const unsigned n_leaves) {
+__global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __restrict__ jobs,
+                                                              const unsigned long long* __restrict__ leaf_off,
+                                                              const unsigned n_jobs, const unsigned cap_max) {
     constexpr int U = LeafShape<W>::U, B = LeafShape<W>::B;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_flags;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long total = leaf_off[n_jobs];
 
     Table t;
     t.stride = cap_max;
@@ -199,27 +203,56 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job j, cons
     }
     if (threadIdx.x == 0) s_flags = 0;
 
-    unsigned long long windows = 0, distinct = 0;  // this thread's share, added once at the end
-    unsigned leaf = blockIdx.x;
+    // statistics of the current analysis, added when the analysis changes
+    unsigned long long windows = 0, distinct = 0;
+    unsigned stat_job = 0;
+    auto flush_stats = [&](unsigned ji) {
+        unsigned long long d = distinct;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0 && d) atomicAdd(jobs[ji].stats + 1, d);
+        if (threadIdx.x == 0 && windows) atomicAdd(jobs[ji].stats + 0, windows);
+        windows = distinct = 0;
+    };
+
+    unsigned long long g = blockIdx.x;
+    unsigned ji = 0;
+    unsigned leaf = 0;
     LeafInfo li;
     li.ok = false;
     unsigned long long batch[U][W];
-    if (leaf < n_leaves) {
-        li = leaf_info(j, leaf);
+    if (g < total) {
+        ji = job_of(leaf_off, n_jobs, g);
+        leaf = (unsigned)(g - leaf_off[ji]);
+        li = leaf_info(jobs[ji], leaf);
         load_batch<W>(li, 0, batch);
+        stat_job = ji;
     }
     __syncthreads();
 
-    while (leaf < n_leaves) {
-        const unsigned next = leaf + gridDim.x;
+    while (g < total) {
+        const Job& j = jobs[ji];
+        if (ji != stat_job) {
+            flush_stats(stat_job);
+            stat_job = ji;
+        }
+        const unsigned long long ng = g + gridDim.x;
+        unsigned nji = ji, nleaf = 0;
+        if (ng < total) {
+            nji = job_of(leaf_off, n_jobs, ng);
+            nleaf = (unsigned)(ng - leaf_off[nji]);
+        }
         if (!li.ok || li.n >= 65536ull) {
             if (li.ok && threadIdx.x == 0) {  // 16-bit tallies could wrap: exact recount in HBM
                 const unsigned idx = atomicAdd(j.fb_n, 1u);
                 if (idx < j.fb_cap) j.fb_list[idx] = leaf; else set_status(j, ST_FALLBACK_FULL);
             }
-            leaf = next;
-            if (leaf < n_leaves) {
-                li = leaf_info(j, leaf);
+            g = ng;
+            ji = nji;
+            leaf = nleaf;
+            li.ok = false;
+            if (g < total) {
+                li = leaf_info(jobs[ji], leaf);
                 load_batch<W>(li, 0, batch);
             }
             continue;
@@ -242,8 +275,8 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job j, cons
         // the next leaf's first batch loads while this one is swept
         LeafInfo nli;
         nli.ok = false;
-        if (next < n_leaves) {
-            nli = leaf_info(j, next);
+        if (ng < total) {
+            nli = leaf_info(jobs[nji], nleaf);
             load_batch<W>(nli, 0, batch);
         }
         const unsigned per = cap / kLeafWarps;  // a multiple of 32
@@ -321,34 +354,34 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job j, cons
         }
         if (threadIdx.x == 0) s_flags = 0;
         __syncthreads();  // the clean table is reused by the next leaf
-        leaf = next;
+        g = ng;
+        ji = nji;
+        leaf = nleaf;
         li = nli;
     }
-    // per-thread shares of the statistics
-#pragma unroll
-    for (int o = 16; o; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
-    if (lane == 0 && distinct) atomicAdd(j.stats + 1, distinct);
-    if (threadIdx.x == 0 && windows) atomicAdd(j.stats + 0, windows);
+    if (blockIdx.x < total) flush_stats(stat_job);
 }
 
 template <int W>
-static cudaError_t launch_leaf_w(const Job& j, unsigned cap_max, int num_sms, cudaStream_t s) {
+static cudaError_t launch_leaf_w(const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,
+                                 unsigned long long leaves, unsigned cap_max, int num_sms, cudaStream_t s) {
     const size_t smem = leaf_smem_bytes(W, cap_max);
     cudaError_t e = cudaFuncSetAttribute(leaf_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned long long leaves = 1ull << (j.g.p1 + j.g.p2);
     unsigned long long grid = (unsigned long long)num_sms * 2;
     if (grid > leaves) grid = leaves;
-    leaf_kernel<W><<<(unsigned)grid, kLeafThreads, smem, s>>>(j, cap_max, (unsigned)leaves);
+    if (grid == 0) return cudaSuccess;
+    leaf_kernel<W><<<(unsigned)grid, kLeafThreads, smem, s>>>(jobs, leaf_off, n_jobs, cap_max);
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf(const Job& j, unsigned cap_max, int num_sms, cudaStream_t s) {
-    switch (j.g.W) {
-        case 1: return launch_leaf_w<1>(j, cap_max, num_sms, s);
-        case 2: return launch_leaf_w<2>(j, cap_max, num_sms, s);
-        case 3: return launch_leaf_w<3>(j, cap_max, num_sms, s);
-        case 4: return launch_leaf_w<4>(j, cap_max, num_sms, s);
+cudaError_t launch_leaf(unsigned W, const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,
+                        unsigned long long leaves, unsigned cap_max, int num_sms, cudaStream_t s) {
+    switch (W) {
+        case 1: return launch_leaf_w<1>(jobs, leaf_off, n_jobs, leaves, cap_max, num_sms, s);
+        case 2: return launch_leaf_w<2>(jobs, leaf_off, n_jobs, leaves, cap_max, num_sms, s);
+        case 3: return launch_leaf_w<3>(jobs, leaf_off, n_jobs, leaves, cap_max, num_sms, s);
+        case 4: return launch_leaf_w<4>(jobs, leaf_off, n_jobs, leaves, cap_max, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

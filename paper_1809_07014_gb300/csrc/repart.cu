@@ -16,9 +16,13 @@ __host__ __device__ inline unsigned repart_tile(unsigned W) {
     return W == 1 ? RepartShape<1>::S : (W == 2 ? RepartShape<2>::S : RepartShape<3>::S);
 }
 
-// One CTA: per bucket the records it really holds, its level-2 tile count and
-// (uniform mode) the capacity of each of its leaves, then exclusive prefixes.
-__global__ void __launch_bounds__(kStageThreads) l2_plan_kernel(const Job j, unsigned long long l2_capacity) {
+// One CTA per analysis: per bucket the records it really holds, its level-2
+// tile count and (uniform mode) the capacity of each of its leaves, then
+// exclusive prefixes.
+__global__ void __launch_bounds__(kStageThreads) l2_plan_kernel(const Job* __restrict__ jobs) {
+    const Job& j = jobs[blockIdx.x];
+    if (j.g.p2 == 0) return;
+    const unsigned long long l2_capacity = j.l2_capacity;
     __shared__ unsigned long long warp_tmp[8];
     __shared__ unsigned long long s_tiles, s_slots;
     const unsigned P1 = 1u << j.g.p1, P2 = 1u << j.g.p2;
@@ -76,21 +80,47 @@ struct L2Dest {
     }
 };
 
+// Level-2 tiles of every analysis before analysis i (one CTA).
+__global__ void __launch_bounds__(kStageThreads) job_tiles_kernel(const Job* __restrict__ jobs, const unsigned n_jobs,
+                                                                   unsigned long long* __restrict__ job_tile_off) {
+    __shared__ unsigned long long warp_tmp[8];
+    __shared__ unsigned long long s_run;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (unsigned base = 0; base < n_jobs; base += kStageThreads) {
+        const unsigned i = base + threadIdx.x;
+        unsigned long long t = 0;
+        if (i < n_jobs) {
+            const Job& jb = jobs[i];
+            // an analysis whose planner overflowed contributes no tiles (the host retries it)
+            if (jb.g.p2 && !(*(volatile unsigned*)jb.status & ST_L2_PLAN)) t = jb.tile_prefix[1u << jb.g.p1];
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_scan_u64(t, warp_tmp, &tot);
+        if (i < n_jobs) job_tile_off[i] = s_run + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) s_run += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) job_tile_off[n_jobs] = s_run;
+}
+
 template <int W, unsigned MAXPER>
-__global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job j) {
+__global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __restrict__ jobs,
+                                                                 const unsigned long long* __restrict__ job_tile_off,
+                                                                 const unsigned n_jobs) {
     constexpr unsigned S = RepartShape<W>::S;
     extern __shared__ __align__(16) unsigned char smem[];
-    const unsigned P1 = 1u << j.g.p1, P2 = 1u << j.g.p2;
-    StageBufs b = carve_stage(smem, W, S, P2);
-    for (unsigned d = threadIdx.x; d < P2; d += kStageThreads) b.hist[d] = 0;
-    __syncthreads();
-    const unsigned zb = j.g.zl_bits();
-    // the planner found the leaf layout larger than the buffer: write nothing, the host retries
-    // (only the planner's bit: leaf overflows found by other CTAs must not stop the
-    // counting, the host needs complete per-leaf totals for the exact layout)
-    if (*(volatile unsigned*)j.status & ST_L2_PLAN) return;
-    const unsigned long long total = j.tile_prefix[P1];
-    for (unsigned long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const unsigned long long all = job_tile_off[n_jobs];
+    for (unsigned long long gt = blockIdx.x; gt < all; gt += gridDim.x) {
+        const unsigned ji = job_of(job_tile_off, n_jobs, gt);
+        const Job& j = jobs[ji];
+        const unsigned long long tile = gt - job_tile_off[ji];
+        const unsigned P1 = 1u << j.g.p1, P2 = 1u << j.g.p2;
+        StageBufs b = carve_stage(smem, W, S, P2);
+        for (unsigned d = threadIdx.x; d < P2; d += kStageThreads) b.hist[d] = 0;
+        __syncthreads();
+        const unsigned zb = j.g.zl_bits();
         // bucket of this tile: last b with tile_prefix[b] <= tile
         unsigned lo = 0, hi = P1 - 1;
         while (lo < hi) {
@@ -135,33 +165,39 @@ size_t repart_smem_bytes(unsigned W, unsigned p2) {
     return stage_smem_bytes(W, repart_tile(W), 1u << p2);
 }
 
-cudaError_t launch_l2_plan(const Job& j, unsigned long long l2_capacity, cudaStream_t s) {
-    l2_plan_kernel<<<1, kStageThreads, 0, s>>>(j, l2_capacity);
+cudaError_t launch_l2_plan(const Job* jobs, unsigned n_jobs, unsigned long long* job_tile_off, cudaStream_t s) {
+    if (n_jobs == 0) return cudaSuccess;
+    l2_plan_kernel<<<n_jobs, kStageThreads, 0, s>>>(jobs);
+    job_tiles_kernel<<<1, kStageThreads, 0, s>>>(jobs, n_jobs, job_tile_off);
     return cudaGetLastError();
 }
 
 template <int W, unsigned MAXPER>
-static cudaError_t launch_repart_wp(const Job& j, int num_sms, cudaStream_t s) {
-    const size_t smem = repart_smem_bytes(W, j.g.p2);
+static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
+                                    unsigned max_p2, int num_sms, cudaStream_t s) {
+    const size_t smem = repart_smem_bytes(W, max_p2);
     cudaError_t e =
         cudaFuncSetAttribute(repart_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(j);
+    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(jobs, job_tile_off, n_jobs);
     return cudaGetLastError();
 }
 
 template <int W>
-static cudaError_t launch_repart_w(const Job& j, int num_sms, cudaStream_t s) {
-    if ((1u << j.g.p2) <= 2 * kStageThreads) return launch_repart_wp<W, 2>(j, num_sms, s);
-    return launch_repart_wp<W, kMaxStageDest / kStageThreads>(j, num_sms, s);
+static cudaError_t launch_repart_w(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
+                                   unsigned max_p2, int num_sms, cudaStream_t s) {
+    if ((1u << max_p2) <= 2 * kStageThreads)
+        return launch_repart_wp<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+    return launch_repart_wp<W, kMaxStageDest / kStageThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
 }
 
-cudaError_t launch_repart(const Job& j, int num_sms, cudaStream_t s) {
-    switch (j.g.W) {
-        case 1: return launch_repart_w<1>(j, num_sms, s);
-        case 2: return launch_repart_w<2>(j, num_sms, s);
-        case 3: return launch_repart_w<3>(j, num_sms, s);
-        case 4: return launch_repart_w<4>(j, num_sms, s);
+cudaError_t launch_repart(unsigned W, const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
+                          unsigned max_p2, int num_sms, cudaStream_t s) {
+    switch (W) {
+        case 1: return launch_repart_w<1>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        case 2: return launch_repart_w<2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        case 3: return launch_repart_w<3>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        case 4: return launch_repart_w<4>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

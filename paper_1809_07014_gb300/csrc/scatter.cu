@@ -24,12 +24,12 @@ struct L1Dest {
     __device__ unsigned long long cap(unsigned d) const { return __ldg(capp + d); }
 };
 
+// One CTA: 256 consecutive reads of job j (a read tile).
 // MAXPER: destinations handled by one thread in a flush (fan-out / 256).
 template <int W, unsigned MAXPER>
-__global__ void __launch_bounds__(kStageThreads, W == 1 ? 3 : 2)
-scatter_kernel(const Job j, const unsigned long long r0, const unsigned long long r1) {
+__device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long long r0, const unsigned long long r1,
+                                             unsigned char* smem) {
     constexpr unsigned R = ScatterShape<W>::R, S = ScatterShape<W>::S;
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_maxlen;
     const unsigned P = 1u << j.g.p1;
     StageBufs b = carve_stage(smem, W, S, P);
@@ -37,7 +37,7 @@ scatter_kernel(const Job j, const unsigned long long r0, const unsigned long lon
     for (unsigned d = threadIdx.x; d < P; d += kStageThreads) b.hist[d] = 0;
     __syncthreads();
 
-    const unsigned long long r = r0 + (unsigned long long)blockIdx.x * kStageThreads + threadIdx.x;
+    const unsigned long long r = r0 + threadIdx.x;
     Roll<W> roll;
     unsigned long long L = 0;
     const bool have = r < r1;
@@ -50,6 +50,8 @@ scatter_kernel(const Job j, const unsigned long long r0, const unsigned long lon
     const unsigned long long steps = (unsigned long long)s_maxlen + 1;
     const unsigned long long rounds = (steps + R - 1) / R;
     L1Dest dest{j.l1_fill, j.l1_start, j.l1_cap};
+    const Geometry g = j.g;
+    const unsigned pass = j.pass;
     unsigned emitted = 0;
     for (unsigned long long round = 0; round < rounds; ++round) {
 #pragma unroll 1
@@ -60,7 +62,7 @@ scatter_kernel(const Job j, const unsigned long long r0, const unsigned long lon
             if (have && t <= L) {
                 unsigned long long key[W], rec[W];
                 unsigned lc = 0, rc = 0, bucket = 0;
-                if (roll.step(t, key, lc, rc) && make_record<W>(j.g, j.pass, key, lc, rc, rec, bucket)) {
+                if (roll.step(t, key, lc, rc) && make_record<W>(g, pass, key, lc, rc, rec, bucket)) {
                     const unsigned rank = atomicAdd(&b.hist[bucket], 1u);
 #pragma unroll
                     for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[w];
@@ -72,10 +74,23 @@ scatter_kernel(const Job j, const unsigned long long r0, const unsigned long lon
         }
         flush_stage<W, MAXPER>(b, S, P, dest, j.l1_rec, j.status, ST_L1_OVERFLOW);
     }
-    // windows emitted into this pass (a check against the leaves' totals)
+    // windows emitted into this pass (checked against the windows the leaves count)
 #pragma unroll
     for (int o = 16; o; o >>= 1) emitted += __shfl_xor_sync(0xffffffffu, emitted, o);
     if ((threadIdx.x & 31) == 0 && emitted) atomicAdd(j.stats + 2, (unsigned long long)emitted);
+}
+
+// One CTA per read tile over all jobs (all of key width W).
+template <int W, unsigned MAXPER>
+__global__ void __launch_bounds__(kStageThreads, W == 1 ? 3 : 2)
+scatter_kernel(const Job* __restrict__ jobs, const unsigned long long* __restrict__ tile_off, const unsigned n_jobs) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned long long t = blockIdx.x;
+    const unsigned ji = job_of(tile_off, n_jobs, t);
+    const Job& j = jobs[ji];
+    const unsigned long long r0 = (t - tile_off[ji]) * kStageThreads;
+    const unsigned long long r1 = r0 + kStageThreads < j.n_reads ? r0 + kStageThreads : j.n_reads;
+    scatter_tile<W, MAXPER>(j, r0, r1, smem);
 }
 
 size_t scatter_smem_bytes(unsigned W, unsigned p1) {
@@ -89,31 +104,32 @@ size_t scatter_smem_bytes(unsigned W, unsigned p1) {
 }
 
 template <int W, unsigned MAXPER>
-static cudaError_t launch_scatter_wp(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
-    const size_t smem = scatter_smem_bytes(W, j.g.p1);
+static cudaError_t launch_scatter_wp(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                                     unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+    const size_t smem = scatter_smem_bytes(W, max_p1);
     cudaError_t e =
         cudaFuncSetAttribute(scatter_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned long long n = r1 - r0;
-    const unsigned long long grid = (n + kStageThreads - 1) / kStageThreads;
-    if (grid == 0) return cudaSuccess;
-    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    scatter_kernel<W, MAXPER><<<(unsigned)grid, kStageThreads, smem, s>>>(j, r0, r1);
+    if (tiles == 0) return cudaSuccess;
+    if (tiles > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    scatter_kernel<W, MAXPER><<<(unsigned)tiles, kStageThreads, smem, s>>>(jobs, tile_off, n_jobs);
     return cudaGetLastError();
 }
 
 template <int W>
-static cudaError_t launch_scatter_w(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
-    if ((1u << j.g.p1) <= 2 * kStageThreads) return launch_scatter_wp<W, 2>(j, r0, r1, s);
-    return launch_scatter_wp<W, kMaxStageDest / kStageThreads>(j, r0, r1, s);
+static cudaError_t launch_scatter_w(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                                    unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+    if ((1u << max_p1) <= 2 * kStageThreads) return launch_scatter_wp<W, 2>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+    return launch_scatter_wp<W, kMaxStageDest / kStageThreads>(jobs, tile_off, n_jobs, tiles, max_p1, s);
 }
 
-cudaError_t launch_scatter(const Job& j, unsigned long long r0, unsigned long long r1, cudaStream_t s) {
-    switch (j.g.W) {
-        case 1: return launch_scatter_w<1>(j, r0, r1, s);
-        case 2: return launch_scatter_w<2>(j, r0, r1, s);
-        case 3: return launch_scatter_w<3>(j, r0, r1, s);
-        case 4: return launch_scatter_w<4>(j, r0, r1, s);
+cudaError_t launch_scatter(unsigned W, const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                           unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+    switch (W) {
+        case 1: return launch_scatter_w<1>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+        case 2: return launch_scatter_w<2>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+        case 3: return launch_scatter_w<3>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+        case 4: return launch_scatter_w<4>(jobs, tile_off, n_jobs, tiles, max_p1, s);
     }
     return cudaErrorInvalidValue;
 }
