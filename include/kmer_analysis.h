@@ -98,7 +98,8 @@ typedef struct {
     uint64_t memory_budget;  /* device bytes the analysis may hold while querying; 0 = 85% of free memory */
     uint32_t leaf_bits;      /* tuning override: log2 of the number of partitions (0 = automatic) */
     uint32_t flags;          /* KMER_FLAG_* */
-    uint32_t reserved[4];    /* must be zero */
+    uint32_t l1_bits;        /* tuning override: log2 of the first-level fan-out when two levels are used (0 = automatic) */
+    uint32_t reserved[3];    /* must be zero */
 } kmer_analysis_params;
 
 /* flags: record CUDA events around each stage on the analysis stream and
@@ -211,6 +212,50 @@ int kmer_analysis_reset(kmer_analysis_t *h);
 
 /* Releases the analysis and every buffer it owns.  NULL is accepted. */
 int kmer_analysis_destroy(kmer_analysis_t *h);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent analyses (samples of uneven size, mixed k) run together
+ * (Algorithm 1 runs K-merAnalysis once per k; a sample collection runs it
+ * once per sample).  Each job is one readset with its own parameters and
+ * gives exactly the result of a separate create/submit/query.  The jobs are
+ * grouped into waves whose scratch fits the memory budget; each wave is
+ * captured once as a CUDA graph in which every stage is one launch over all
+ * jobs of a key width, and kmer_batch_run replays the graphs.  A job whose
+ * buffers turn out too small (or that is too large for any wave) is re-run
+ * alone through the regular path, so results are always exact. */
+typedef struct kmer_batch kmer_batch_t;
+
+typedef struct {
+    const kmer_readset_t *readset;  /* must outlive the batch and keep its size */
+    kmer_analysis_params params;    /* variant must be KMER_VARIANT_PARTITIONED; distinct_hint, leaf_bits and
+                                       l1_bits size the job's partitions (an autotuner can set them) */
+    uint64_t survivors_hint;        /* expected surviving k-mers, sizes the output (0 = a quarter of the windows) */
+} kmer_batch_job;
+
+typedef struct {
+    uint32_t jobs, waves;
+    uint32_t graph_launches;  /* by the last run: one per wave */
+    uint32_t jobs_alone;      /* jobs of the last run that went through the regular path */
+    float ms_total;           /* wall time of the last run, host clock */
+} kmer_batch_stats;
+
+/* Plans the jobs, allocates every buffer (memory_budget bytes of device
+ * memory at most; 0 = 60% of free memory) and captures the graphs.  The
+ * stream is used for every run.  Errors: INVALID_ARG (NULL, bad parameters,
+ * readset/quality mismatch), NO_DEVICE, OOM, CUDA. */
+int kmer_batch_create(const kmer_batch_job *jobs, uint32_t n_jobs, uint64_t memory_budget, void *cuda_stream,
+                      kmer_batch_t **out);
+/* Runs every job (one graph launch per wave) and synchronises the stream.
+ * The readsets may be re-packed between runs with reads of the same sizes. */
+int kmer_batch_run(kmer_batch_t *b);
+/* Device view of job `job`'s survivors after a run (as kmer_analysis_query);
+ * valid until the next run or destroy.  Errors: INVALID_ARG, BAD_STATE. */
+int kmer_batch_result(kmer_batch_t *b, uint32_t job, kmer_result_view *out);
+/* Host copy of job `job`'s survivors (as kmer_analysis_copy_results). */
+int kmer_batch_copy_results(kmer_batch_t *b, uint32_t job, uint64_t *keys, uint32_t *count, uint32_t *ext,
+                            uint8_t *cls, uint64_t capacity);
+int kmer_batch_get_stats(const kmer_batch_t *b, kmer_batch_stats *out);
+int kmer_batch_destroy(kmer_batch_t *b);
 
 /* k-mer analysis without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

@@ -51,7 +51,7 @@ class kmer_analysis_params(ctypes.Structure):
                 ("err_num", ctypes.c_uint32), ("err_den", ctypes.c_uint32), ("t_ext", ctypes.c_uint32),
                 ("variant", ctypes.c_uint32), ("distinct_hint", ctypes.c_uint64),
                 ("memory_budget", ctypes.c_uint64), ("leaf_bits", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+                ("flags", ctypes.c_uint32), ("l1_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class kmer_result_view(ctypes.Structure):
@@ -75,6 +75,18 @@ class kmer_analysis_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class kmer_batch_job(ctypes.Structure):
+    _fields_ = [("readset", ctypes.c_void_p), ("params", kmer_analysis_params), ("survivors_hint", ctypes.c_uint64)]
+
+
+class kmer_batch_stats(ctypes.Structure):
+    _fields_ = [("jobs", ctypes.c_uint32), ("waves", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32),
+                ("jobs_alone", ctypes.c_uint32), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # exported symbol -> (restype, argtypes)
 _vp, _u32, _u64, _int = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 _SIGNATURES = {
@@ -92,6 +104,12 @@ _SIGNATURES = {
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
+    "kmer_batch_create": (_int, [ctypes.POINTER(kmer_batch_job), _u32, _u64, _vp, ctypes.POINTER(_vp)]),
+    "kmer_batch_run": (_int, [_vp]),
+    "kmer_batch_result": (_int, [_vp, _u32, ctypes.POINTER(kmer_result_view)]),
+    "kmer_batch_copy_results": (_int, [_vp, _u32, _vp, _vp, _vp, _vp, _u64]),
+    "kmer_batch_get_stats": (_int, [_vp, ctypes.POINTER(kmer_batch_stats)]),
+    "kmer_batch_destroy": (_int, [_vp]),
     "kmer_analysis_run_noalloc": (_int, [_vp, _vp, _vp, _u64, ctypes.POINTER(kmer_analysis_params), _vp, _vp, _vp,
                                          _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "kmer_strerror": (ctypes.c_char_p, [_int]),
@@ -213,6 +231,39 @@ def kmer_analysis_run_noalloc(bases: int, quals: int, offsets: int, n_reads: int
                                                     count, ext, cls, capacity, ctypes.byref(n), stream or None),
            "kmer_analysis_run_noalloc")
     return n.value
+
+
+def kmer_batch_create(jobs, memory_budget: int = 0, stream: int = 0) -> int:
+    arr = (kmer_batch_job * max(1, len(jobs)))(*jobs)
+    out = _vp()
+    _check(load_library().kmer_batch_create(arr, len(jobs), memory_budget, stream or None, ctypes.byref(out)),
+           "kmer_batch_create")
+    return out.value
+
+
+def kmer_batch_run(b: int) -> None:
+    _check(load_library().kmer_batch_run(b), "kmer_batch_run")
+
+
+def kmer_batch_result(b: int, job: int) -> kmer_result_view:
+    v = kmer_result_view()
+    _check(load_library().kmer_batch_result(b, job, ctypes.byref(v)), "kmer_batch_result")
+    return v
+
+
+def kmer_batch_copy_results(b: int, job: int, keys: int, count: int, ext: int, cls: int, capacity: int) -> None:
+    _check(load_library().kmer_batch_copy_results(b, job, keys, count, ext, cls, capacity),
+           "kmer_batch_copy_results")
+
+
+def kmer_batch_get_stats(b: int) -> kmer_batch_stats:
+    st = kmer_batch_stats()
+    _check(load_library().kmer_batch_get_stats(b, ctypes.byref(st)), "kmer_batch_get_stats")
+    return st
+
+
+def kmer_batch_destroy(b: int) -> None:
+    _check(load_library().kmer_batch_destroy(b), "kmer_batch_destroy")
 
 
 def kmer_strerror(code: int) -> str:
@@ -366,3 +417,52 @@ class KmerAnalysis:
         except Exception:
             pass
 
+
+
+class Batch:
+    """Many analyses run together (kmer_batch_*): jobs are (ReadSet, params) pairs,
+    params given as keyword dicts over kmer_analysis_params fields (``k`` required)
+    plus an optional ``survivors_hint``."""
+
+    def __init__(self, jobs, memory_budget: int = 0, stream=None):
+        cj = []
+        self._keep = []
+        for rs, kw in jobs:
+            kw = dict(kw)
+            hint = int(kw.pop("survivors_hint", 0))
+            k = kw.pop("k")
+            cj.append(kmer_batch_job(rs.handle, make_params(k, **kw), hint))
+            self._keep.append(rs)
+        self.n = len(cj)
+        self.handle = kmer_batch_create(cj, memory_budget, _stream_of(stream))
+
+    def run(self):
+        kmer_batch_run(self.handle)
+
+    def view(self, i: int) -> kmer_result_view:
+        return kmer_batch_result(self.handle, i)
+
+    def results(self, i: int) -> Result:
+        v = self.view(i)
+        n, W = int(v.n), int(v.words)
+        keys = np.empty((n, W), dtype=np.uint64)
+        count = np.empty(n, dtype=np.uint32)
+        ext = np.empty((n, 8), dtype=np.uint32)
+        cls = np.empty((n, 2), dtype=np.uint8)
+        kmer_batch_copy_results(self.handle, i, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
+        return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def stats(self) -> dict:
+        return kmer_batch_get_stats(self.handle).as_dict()
+
+    def close(self):
+        if self.handle:
+            kmer_batch_destroy(self.handle)
+            self.handle = 0
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

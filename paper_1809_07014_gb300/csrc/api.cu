@@ -18,9 +18,12 @@
 
 using namespace kmer;
 
-namespace {
+#include "host.h"
 
+namespace kmer {
+namespace {
 thread_local std::string g_err;
+}  // namespace
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -32,85 +35,53 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-#define CK(call)                                                                                         \
-    do {                                                                                                 \
-        cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess)                                                                           \
-            return fail(e_ == cudaErrorMemoryAllocation ? KMER_ERR_OOM : KMER_ERR_CUDA, "%s: %s (%s:%d)", \
-                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
-    } while (0)
+const char* last_error_message() { return g_err.c_str(); }
 
-#define TRY(call)                \
-    do {                         \
-        int rc_ = (call);        \
-        if (rc_ != KMER_OK) return rc_; \
-    } while (0)
-
-// Grow-only device buffer.
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    int ensure(size_t n) {
-        if (n <= bytes && p) return KMER_OK;
-        release();
-        if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            bytes = 0;
-            cudaGetLastError();
-            return fail(KMER_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
-        }
-        bytes = n;
-        return KMER_OK;
+Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits) {
+    Geometry g{};
+    g.k = k;
+    g.W = (2 * k + 63) / 64;
+    g.hb = 2 * k - 64 * (g.W - 1);
+    g.bt = g.W == 1 ? 2 * k : 64;
+    // about half a leaf table of distinct keys per leaf
+    const unsigned long long target = std::max(64u, cap_max / 2);
+    unsigned p = leaf_bits ? leaf_bits : ceil_log2((basis + target - 1) / target);
+    const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
+    p = std::max(p, need);
+    p = std::min(p, g.bt);
+    // passes: records of one pass (two levels, with slack) must fit the budget
+    const double rec_bytes = 8.0 * g.W;
+    unsigned ps = 0;
+    for (;;) {
+        const double win = (double)windows / (double)(1ull << ps);
+        const double bytes = win * rec_bytes * 3.5 + 64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
+        if (bytes <= 0.8 * (double)budget || ps >= p || ps >= 12) break;
+        ++ps;
     }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
+    const unsigned lb = p - ps;
+    unsigned p1, p2;
+    if (lb <= 11) {
+        p1 = lb;
+        p2 = 0;
+    } else {
+        // the scatter's cost grows with its fan-out more than the repartition's does
+        p1 = std::min(11u, lb / 2);
+        if (l1_bits >= 1 && l1_bits <= 11 && l1_bits < lb) p1 = l1_bits;
+        p2 = lb - p1;
+        if (p2 > 11) p2 = 11;
     }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-struct Misc {  // small device counters read back after each pass
-    unsigned long long out_n;
-    unsigned long long stats[4];
-    unsigned int status;
-    unsigned int fb_n;
-};
-
-unsigned long long next_pow2(unsigned long long x) {
-    unsigned long long p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-unsigned ceil_log2(unsigned long long x) {
-    unsigned b = 0;
-    while ((1ull << b) < x) ++b;
-    return b;
+    if (ps + p1 < need) p1 = need - ps;
+    g.ps = ps;
+    g.p1 = p1;
+    g.p2 = p2;
+    return g;
 }
 
-}  // namespace
+}  // namespace kmer
 
-struct kmer_readset {
-    int device = 0;
-    unsigned long long n_reads = 0, n_bases = 0, n_blocks = 0;
-    unsigned qual_offset = 33, qual_threshold = 20;
-    DevBuf blocks, blk_off, offsets;
-    DevBuf tmp_bases, tmp_quals, nblk, scratch, stats;  // reused by re-packs
-    unsigned launches = 0;
-    unsigned long long len_stats[kLenHist] = {};
+using namespace kmer;
 
-    // Exact number of k-windows (before N filtering) for this k.
-    unsigned long long windows_for(unsigned k) const {
-        unsigned long long w = 0;
-        for (unsigned L = k; L < (unsigned)kLenExact; ++L) w += len_stats[L] * (L - k + 1);
-        const unsigned long long big_n = len_stats[kLenExact], big_sum = len_stats[kLenExact + 1];
-        if (big_n) w += big_sum - (unsigned long long)(k - 1) * big_n;
-        return w;
-    }
-};
 
 struct kmer_analysis {
     kmer_analysis_params p{};
@@ -167,6 +138,7 @@ int validate_params(const kmer_analysis_params* p) {
     if (p->qual_offset > 255 || p->qual_threshold > 255)
         return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
     if (p->leaf_bits > 22) return fail(KMER_ERR_INVALID_ARG, "leaf_bits must be <= 22");
+    if (p->l1_bits > 11) return fail(KMER_ERR_INVALID_ARG, "l1_bits must be <= 11");
     if (p->flags & ~KMER_FLAG_PROFILE) return fail(KMER_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
     for (unsigned r : p->reserved)
         if (r) return fail(KMER_ERR_INVALID_ARG, "reserved fields must be zero");
@@ -291,50 +263,16 @@ struct Plan {
 
 Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget, unsigned cap_max) {
     Plan pl{};
-    Geometry& g = pl.g;
-    g.k = h->p.k;
-    g.W = (2 * g.k + 63) / 64;
-    g.hb = 2 * g.k - 64 * (g.W - 1);
-    g.bt = g.W == 1 ? 2 * g.k : 64;
     pl.windows = windows;
     unsigned long long basis = windows;
     if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
     else if (h->hist_k == h->p.k && h->hist_ratio > 0.0)  // learned from the previous query at this k
         basis = std::min<unsigned long long>(windows, (unsigned long long)(1.15 * h->hist_ratio * (double)windows) + 1);
-    const unsigned long long target = std::max(64u, cap_max / 2);
-    unsigned p = h->p.leaf_bits ? h->p.leaf_bits : ceil_log2((basis + target - 1) / target);
-    const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
-    p = std::max(p, need);
-    p = std::min(p, g.bt);
-    // passes: records of one pass (two levels, with slack) must fit the budget
-    const double rec_bytes = 8.0 * g.W;
-    unsigned ps = 0;
-    for (;;) {
-        const double win = (double)windows / (double)(1ull << ps);
-        const double bytes = win * rec_bytes * 2.6 + 64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
-        if (bytes <= 0.8 * (double)budget || ps >= p || ps >= 12) break;
-        ++ps;
-    }
-    const unsigned lb = p - ps;
-    unsigned p1, p2;
-    if (lb <= 11) {
-        p1 = lb;
-        p2 = 0;
-    } else {
-        // the scatter's cost grows with its fan-out more than the repartition's does
-        p1 = std::min(11u, lb / 2);
-        if (const char* e = getenv("KMER_L1_BITS")) {  // tuning experiments only
-            const int v = atoi(e);
-            if (v >= 1 && v <= 11 && (unsigned)v < lb) p1 = (unsigned)v;
-        }
-        p2 = lb - p1;
-        if (p2 > 11) { p2 = 11; }
-    }
-    if (ps + p1 < need) p1 = need - ps;
-    g.ps = ps;
-    g.p1 = p1;
-    g.p2 = p2;
-    pl.passes = 1u << ps;
+    unsigned l1 = h->p.l1_bits;
+    if (!l1)
+        if (const char* e = getenv("KMER_L1_BITS")) l1 = (unsigned)atoi(e);  // tuning experiments only
+    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, l1);
+    pl.passes = 1u << pl.g.ps;
     return pl;
 }
 
@@ -984,7 +922,7 @@ const char* kmer_strerror(int code) {
     return "unknown error";
 }
 
-const char* kmer_last_error_message(void) { return g_err.c_str(); }
+const char* kmer_last_error_message(void) { return kmer::last_error_message(); }
 
 const char* kmer_version(void) { return "1.0.0"; }
 

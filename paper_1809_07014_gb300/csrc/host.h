@@ -1,0 +1,117 @@
+// Host-side internals shared by the C-ABI implementation files (not part of
+// the public interface): error reporting, grow-only device buffers, the
+// packed readset, small device counters and the planning of one analysis.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "kmer_analysis.h"
+
+namespace kmer {
+
+// Records `code` with a formatted detail for kmer_last_error_message().
+int fail(int code, const char* fmt, ...);
+const char* last_error_message();
+
+#define CK(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return ::kmer::fail(e_ == cudaErrorMemoryAllocation ? KMER_ERR_OOM : KMER_ERR_CUDA,          \
+                                "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
+    } while (0)
+
+#define TRY(call)                       \
+    do {                                \
+        int rc_ = (call);               \
+        if (rc_ != KMER_OK) return rc_; \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    int ensure(size_t n) {
+        if (n <= bytes && p) return KMER_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            bytes = 0;
+            cudaGetLastError();
+            return fail(KMER_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return KMER_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct Misc {  // small device counters read back after each pass
+    unsigned long long out_n;
+    unsigned long long stats[4];
+    unsigned int status;
+    unsigned int fb_n;
+};
+
+inline unsigned long long next_pow2(unsigned long long x) {
+    unsigned long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+inline unsigned ceil_log2(unsigned long long x) {
+    unsigned b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+// Partition geometry for one analysis: k-mer words, pass bits and level bits.
+// basis = expected distinct keys (or windows), cap_max = leaf table slots,
+// leaf_bits / l1_bits = overrides (0 = automatic).
+Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits);
+
+}  // namespace kmer
+
+struct kmer_readset {
+    int device = 0;
+    unsigned long long n_reads = 0, n_bases = 0, n_blocks = 0;
+    unsigned qual_offset = 33, qual_threshold = 20;
+    kmer::DevBuf blocks, blk_off, offsets;
+    kmer::DevBuf tmp_bases, tmp_quals, nblk, scratch, stats;  // reused by re-packs
+    unsigned launches = 0;
+    unsigned long long len_stats[kmer::kLenHist] = {};
+
+    // Exact number of k-windows (before N filtering) for this k.
+    unsigned long long windows_for(unsigned k) const {
+        unsigned long long w = 0;
+        for (unsigned L = k; L < (unsigned)kmer::kLenExact; ++L) w += len_stats[L] * (L - k + 1);
+        const unsigned long long big_n = len_stats[kmer::kLenExact], big_sum = len_stats[kmer::kLenExact + 1];
+        if (big_n) w += big_sum - (unsigned long long)(k - 1) * big_n;
+        return w;
+    }
+};

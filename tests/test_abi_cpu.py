@@ -47,12 +47,12 @@ def test_default_params(lib):
     p = pkg.kmer_analysis_default_params(31)
     assert (p.k, p.min_count, p.qual_offset, p.qual_threshold) == (31, 2, 33, 20)
     assert (p.ext_mode, p.t_base, p.err_num, p.err_den, p.t_ext, p.variant) == (0, 2, 1, 10, 2, 0)
-    assert ctypes.sizeof(pkg.kmer_analysis_params) == 4 * 10 + 8 + 8 + 4 + 4 + 4 * 4  # no padding: 80 bytes
+    assert ctypes.sizeof(pkg.kmer_analysis_params) == 4 * 10 + 8 + 8 + 4 + 4 + 4 + 4 * 3  # no padding: 80 bytes
 
 
 @pytest.mark.parametrize("field,value", [
     ("k", 0), ("k", 2), ("k", 128), ("k", 129), ("min_count", 0), ("err_den", 0), ("ext_mode", 2),
-    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 2),
+    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 2), ("l1_bits", 12),
 ])
 def test_invalid_params_rejected_before_device(lib, field, value):
     p = pkg.make_params(31)

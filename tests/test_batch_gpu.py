@@ -1,0 +1,102 @@
+"""Batched analyses (many samples, uneven sizes, mixed k) give, job by job,
+exactly the regular create/submit/query result -- and the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1809_07014_gb300 as pkg
+from tests.helpers import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+def sample(i, n_reads):
+    return synth.generate(synth.metagenome_sample(i, n_reads * 150, n_genomes=3 + i % 5).scaled(
+        n_reads, genome_len_min=20_000 + 7000 * i, genome_len_max=40_000 + 9000 * i))
+
+
+@pytest.fixture(scope="module")
+def samples():
+    import torch
+    assert torch.cuda.is_available()
+    sizes = [300, 5000, 1200, 20000, 800, 9000, 150, 3000]
+    return [sample(i, n) for i, n in enumerate(sizes)]
+
+
+def regular(rs_obj, k):
+    ka = pkg.KmerAnalysis(k)
+    ka.submit(rs_obj)
+    r = ka.results()
+    ka.close()
+    return r
+
+
+def same_result(a, b):
+    ka, kb = a.keys, b.keys
+    oa = np.lexsort(ka.T[::-1]) if len(ka) else np.arange(0)
+    ob = np.lexsort(kb.T[::-1]) if len(kb) else np.arange(0)
+    assert len(oa) == len(ob)
+    assert np.array_equal(ka[oa], kb[ob]) and np.array_equal(a.count[oa], b.count[ob])
+    assert np.array_equal(a.ext[oa], b.ext[ob]) and np.array_equal(a.cls[oa], b.cls[ob])
+    assert a.windows == b.windows and a.distinct == b.distinct
+
+
+def test_batch_matches_regular_and_oracle(samples):
+    ks = [21, 33, 55, 21, 33, 55, 21, 33]
+    rsets = [pkg.ReadSet(s.bases, s.quals, s.offsets) for s in samples]
+    b = pkg.Batch([(r, {"k": k}) for r, k in zip(rsets, ks)])
+    b.run()
+    st = b.stats()
+    assert st["jobs"] == len(samples) and st["graph_launches"] == st["waves"] >= 1
+    for i, (r, k) in enumerate(zip(rsets, ks)):
+        same_result(b.results(i), regular(r, k))
+    for i in (0, 2, 4):  # a few jobs against the oracle as well
+        s = samples[i]
+        assert_same(b.results(i), oracle.run(s.bases, s.quals, s.offsets, oracle.Params(k=ks[i])), f"job {i}")
+    # replaying the graphs gives the same results
+    first = [b.results(i) for i in range(len(samples))]
+    b.run()
+    for i in range(len(samples)):
+        same_result(b.results(i), first[i])
+    b.close()
+
+
+def test_batch_waves_and_exact_reruns(samples):
+    """A small memory budget splits the jobs into several waves; a tiny survivor
+    hint makes outputs overflow, and those jobs are re-run exactly alone."""
+    ks = [21, 21, 33, 55, 33, 21, 55, 33]
+    rsets = [pkg.ReadSet(s.bases, s.quals, s.offsets) for s in samples]
+    jobs = [(r, {"k": k, "survivors_hint": 1 if i % 3 == 0 else 0}) for i, (r, k) in enumerate(zip(rsets, ks))]
+    b = None
+    for mb in (96, 80, 72, 64, 56, 48, 40):  # the first budget that still holds the outputs but splits the jobs
+        try:
+            cand = pkg.Batch(jobs, memory_budget=mb << 20)
+        except pkg.KmerError as e:
+            assert e.code == pkg.KMER_ERR_OOM
+            continue
+        if cand.stats()["waves"] >= 2:
+            b = cand
+            break
+        cand.close()
+    assert b is not None, "no budget split the jobs into waves"
+    b.run()
+    st = b.stats()
+    assert st["waves"] >= 2 and st["jobs_alone"] >= 1
+    for i, (r, k) in enumerate(zip(rsets, ks)):
+        same_result(b.results(i), regular(r, k))
+    b.close()
+
+
+def test_batch_of_empty_and_tiny_jobs():
+    reads = [(b"ACGTACGTACGTACGTACGTACGTA", b"I" * 25), (b"ACG", b"III")]
+    bases = np.frombuffer(b"".join(x[0] for x in reads), np.uint8).copy()
+    quals = np.frombuffer(b"".join(x[1] for x in reads), np.uint8).copy()
+    offsets = np.array([0, 25, 28], np.uint64)
+    r1 = pkg.ReadSet(bases, quals, offsets)
+    r0 = pkg.ReadSet(np.zeros(0, np.uint8), np.zeros(0, np.uint8), np.zeros(1, np.uint64))
+    b = pkg.Batch([(r0, {"k": 21}), (r1, {"k": 5, "min_count": 1}), (r1, {"k": 127})])
+    b.run()
+    assert len(b.results(0)) == 0 and len(b.results(2)) == 0
+    assert_same(b.results(1), oracle.run(bases, quals, offsets, oracle.Params(k=5, min_count=1)), "tiny")
+    b.close()
