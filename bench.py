@@ -48,6 +48,13 @@ def parse_args():
     ap.add_argument("--reads", type=int, default=0, help="override the number of reads (development only)")
     ap.add_argument("--variant", choices=["partitioned", "hbm_table"], default="partitioned")
     ap.add_argument("--leaf-bits", type=int, default=0)
+    ap.add_argument("--mode", choices=["single", "batched", "serve"], default="single",
+                    help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
+                         "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched/serve: scale every sample size")
+    ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
+    ap.add_argument("--large", action="store_true",
+                    help="serve: also run the 15-Gbase, 500-genome instance at k=55 within a 180 GB budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -350,10 +357,221 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- batched
+BATCH_JOBS = 64
+
+
+def batch_workload(scale: float):
+    """64 samples: sizes log-uniform in [5 Mbases, 500 Mbases], k uniform in {21, 33, 55}."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(4)
+    sizes = np.exp(rng.uniform(np.log(5e6), np.log(5e8), BATCH_JOBS)) * scale
+    ks = rng.choice([21, 33, 55], BATCH_JOBS)
+    recipes = []
+    for i, (sz, k) in enumerate(zip(sizes, ks)):
+        r = synth.metagenome_sample(i, int(sz), n_genomes=10 + i % 41)
+        recipes.append((r.scaled(max(1, int(sz) // 150), genome_len_min=500_000, genome_len_max=2_000_000), int(k)))
+    return recipes
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1809_07014_gb300 as pkg
+    from paper_1809_07014_gb300.tune import autotune
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    recipes = batch_workload(args.scale)
+    rsets, ks = [], []
+    t0 = time.perf_counter()
+    for r, k in recipes:
+        s = synth.generate(r)
+        rsets.append(pkg.ReadSet(s.bases, s.quals, s.offsets, stream=stream))
+        ks.append(k)
+    gen_s = time.perf_counter() - t0
+    # one regular query per job: the single-instance baseline on the same GPU
+    windows_all, t_single = 0, 0.0
+    for rs, k in zip(rsets, ks):
+        ka = pkg.KmerAnalysis(k, stream=stream)
+        ka.submit(rs)
+        ka.query()              # warm-up (allocations, learned sizing)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        v = ka.query()
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t1
+        windows_all += int(v.windows)
+        ka.close()
+    # autotune per k on the median-size job of that k
+    tunings = {}
+    for k in sorted(set(ks)):
+        idx = [i for i in range(len(ks)) if ks[i] == k]
+        mid = sorted(idx, key=lambda i: rsets[i].n_bases)[len(idx) // 2]
+        tunings[k] = autotune(rsets[mid], k, reps=1, stream=stream)
+    jobs = []
+    for rs, k in zip(rsets, ks):
+        w = rs.n_bases  # windows of 150-bp reads are ~ (150-k+1)/150 of the bases
+        w = int(w * (150 - k + 1) / 150)
+        jobs.append((rs, tunings[k].params(w)))
+    b = pkg.Batch(jobs, stream=stream)
+    for _ in range(max(1, args.warmup)):
+        b.run()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run()
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t1) / args.steps
+    st = b.stats()
+    line = {"metric": METRIC, "value": windows_all / t_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"batched: {len(jobs)} synthetic metagenome samples, sizes log-uniform "
+                                   f"{5 * args.scale:g}-{500 * args.scale:g} Mbases, k in {{21,33,55}}",
+                       "bases": int(sum(r.n_bases for r in rsets)), "windows": windows_all,
+                       "waves": st["waves"], "jobs_alone": st["jobs_alone"]},
+            "single_instance": {"value": windows_all / t_single, "ms_total": 1e3 * t_single,
+                                "note": "the same jobs, one regular query each, back to back"},
+            "speedup_vs_single_instance": t_single / t_batch,
+            "tuning": {k: {"keys_per_leaf": round(t.keys_per_leaf, 1), "l1_shift": t.l1_shift,
+                           "distinct_ratio": round(t.distinct_ratio, 4)} for k, t in tunings.items()},
+            "setup_s": round(gen_s, 1)}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+# ----------------------------------------------------------------- serving
+def pctl(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=float), q)) if xs else None
+
+
+def run_serve(args):
+    import threading
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1809_07014_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    n_pool = 12
+    sizes = np.exp(rng.uniform(np.log(1e6), np.log(2e9), n_pool)) * args.scale
+    pool = []
+    t0 = time.perf_counter()
+    for i, sz in enumerate(sizes):
+        r = synth.metagenome_sample(5000 + i, int(sz), n_genomes=20)
+        s = synth.generate(r.scaled(max(1, int(sz) // 150), genome_len_min=500_000, genome_len_max=2_000_000))
+        pool.append(pkg.ReadSet(s.bases, s.quals, s.offsets))
+    gen_s = time.perf_counter() - t0
+    kset = [21, 33, 55, 77, 99]
+    reqs = [(int(rng.integers(n_pool)), int(rng.choice(kset))) for _ in range(args.requests)]
+    windows_of = lambda i, k: int(pool[i].n_bases * (150 - k + 1) / 150)
+    # capacity: one request at a time, every request of the plan (warm analyses)
+    srv = pkg.Server(workers=1)
+    for i, k in reqs[:2]:  # warm-up: module loading and first allocations
+        rid = srv.submit(pool[i], k)
+        srv.wait(rid)
+        srv.release(rid)
+    t1 = time.perf_counter()
+    alone_w = 0
+    for i, k in reqs:
+        rid = srv.submit(pool[i], k)
+        v, _ = srv.wait(rid)
+        alone_w += int(v.windows)
+        srv.release(rid)
+    t_alone = time.perf_counter() - t1
+    srv.close()
+    capacity = alone_w / t_alone                    # windows/s, one request at a time
+    # saturated: every request queued at once, 4 workers overlapping on the device
+    srv = pkg.Server(workers=4)
+    t1 = time.perf_counter()
+    sat_ids = [srv.submit(pool[i], k) for i, k in reqs]
+    sat_w = 0
+    for rid in sat_ids:
+        v, _ = srv.wait(rid)
+        sat_w += int(v.windows)
+        srv.release(rid)
+    t_sat = time.perf_counter() - t1
+    peak_sat = srv.stats()["peak_running"]
+    srv.close()
+    mean_w = alone_w / len(reqs)
+    rate = 0.75 * capacity / mean_w                 # requests/s
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+    srv = pkg.Server(workers=4)
+    ids = [None] * len(reqs)
+
+    def client():
+        start = time.perf_counter()
+        at = 0.0
+        for j, (i, k) in enumerate(reqs):
+            at += gaps[j]
+            d = start + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids[j] = srv.submit(pool[i], k)
+
+    th = threading.Thread(target=client)
+    tstart = time.perf_counter()
+    th.start()
+    th.join()
+    lat, first, last, tot_w = [], None, None, 0
+    for j, rid in enumerate(ids):
+        v, info = srv.wait(rid)
+        lat.append(info["t_done_ms"] - info["t_submit_ms"])
+        first = info["t_submit_ms"] if first is None else min(first, info["t_submit_ms"])
+        last = info["t_done_ms"] if last is None else max(last, info["t_done_ms"])
+        tot_w += int(v.windows)
+        srv.release(rid)
+    st = srv.stats()
+    srv.close()
+    span = (last - first) / 1e3
+    line = {"metric": METRIC, "value": tot_w / span, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 0,
+            "ms_per_step": 1e3 * span / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(reqs)} Poisson requests at 75% of measured capacity, sizes "
+                                   f"log-uniform {args.scale:g}-{2000 * args.scale:g} Mbases, k in {kset}",
+                       "pool_bases": int(sum(r.n_bases for r in pool)), "workers": 4},
+            "latency_ms": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "max": max(lat)},
+            "one_at_a_time": {"value": capacity, "note": "the same requests, one worker, back to back"},
+            "saturated": {"value": sat_w / t_sat, "peak_running": peak_sat,
+                          "note": "the same requests all queued at once, 4 workers"},
+            "peak_running": st["peak_running"], "setup_s": round(gen_s, 1)}
+    if args.large:
+        r = synth.Recipe("metagenome-500-genomes-15Gbases", seed=55, n_genomes=500, genome_len_min=1_000_000,
+                         genome_len_max=5_000_000, abundance_sigma=1.5, n_reads=100_000_000, subst_rate=0.01,
+                         err_qual_lo=2, err_qual_hi=12, n_rate=1e-4)
+        t2 = time.perf_counter()
+        s = synth.generate(r)
+        big = pkg.ReadSet(s.bases, s.quals, s.offsets)
+        del s
+        gen2 = time.perf_counter() - t2
+        srv = pkg.Server(memory_budget=180 * 10**9, workers=1)
+        rid = srv.submit(big, 55)
+        v, info = srv.wait(rid)
+        line["large_instance"] = {"bases": big.n_bases, "k": 55, "windows": int(v.windows),
+                                  "distinct": int(v.distinct), "survivors": int(v.n),
+                                  "latency_ms": info["t_done_ms"] - info["t_submit_ms"],
+                                  "k-mers/s": int(v.windows) / ((info["t_done_ms"] - info["t_start_ms"]) / 1e3),
+                                  "budget_bytes": 180 * 10**9, "setup_s": round(gen2, 1)}
+        srv.release(rid)
+        srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -236,6 +236,7 @@ typedef struct {
     uint32_t jobs, waves;
     uint32_t graph_launches;  /* by the last run: one per wave */
     uint32_t jobs_alone;      /* jobs of the last run that went through the regular path */
+    uint32_t fallback_leaves; /* leaves of the last run recounted in an HBM table after their wave */
     float ms_total;           /* wall time of the last run, host clock */
 } kmer_batch_stats;
 
@@ -256,6 +257,52 @@ int kmer_batch_copy_results(kmer_batch_t *b, uint32_t job, uint64_t *keys, uint3
                             uint8_t *cls, uint64_t capacity);
 int kmer_batch_get_stats(const kmer_batch_t *b, kmer_batch_stats *out);
 int kmer_batch_destroy(kmer_batch_t *b);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop: requests (a resident readset + parameters) arrive at any
+ * time from any thread; each is admitted, in arrival order, as soon as its
+ * estimated device footprint fits the memory budget, and runs on one of the
+ * server's worker threads with its own CUDA stream, so admitted requests
+ * overlap on the device.  A finished request holds its results until it is
+ * released; released analyses are pooled per worker and reused by later
+ * requests with the same parameters (evicted when memory is needed).  Every
+ * request gives exactly the result of a separate create/submit/query. */
+typedef struct kmer_server kmer_server_t;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;            /* KMER_OK or the request's error code */
+    uint32_t reserved;
+    double t_submit_ms, t_admit_ms, t_start_ms, t_done_ms;  /* since the server was created */
+    uint64_t footprint_bytes;  /* device memory the request was admitted with */
+} kmer_request_info;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint32_t workers, peak_running;   /* most requests running at the same time */
+    uint32_t pending, running, pooled;
+    uint32_t reserved;
+    uint64_t bytes_in_use, budget;
+} kmer_server_stats;
+
+/* memory_budget: device bytes for all admitted requests (0 = 70% of free
+ * memory); workers: requests that may run at once (1..64). */
+int kmer_server_create(uint64_t memory_budget, uint32_t workers, kmer_server_t **out);
+/* Queues a request (non-blocking).  The readset must stay alive until the
+ * request is released.  p->memory_budget, if nonzero, caps the request's
+ * footprint; a request larger than the budget runs in several passes. */
+int kmer_server_submit(kmer_server_t *s, const kmer_readset_t *rs, const kmer_analysis_params *p, uint64_t *id);
+int kmer_server_poll(kmer_server_t *s, uint64_t id, int *done);
+/* Blocks until the request is done; *out is its device result view (valid
+ * until release), *info its timestamps.  Returns the request's status. */
+int kmer_server_wait(kmer_server_t *s, uint64_t id, kmer_result_view *out, kmer_request_info *info);
+int kmer_server_copy_results(kmer_server_t *s, uint64_t id, uint64_t *keys, uint32_t *count, uint32_t *ext,
+                             uint8_t *cls, uint64_t capacity);
+/* Frees the request's results (its analysis goes back to the pool). */
+int kmer_server_release(kmer_server_t *s, uint64_t id);
+int kmer_server_get_stats(kmer_server_t *s, kmer_server_stats *out);
+/* Waits for admitted requests, drops requests never admitted, frees everything. */
+int kmer_server_destroy(kmer_server_t *s);
 
 /* k-mer analysis without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

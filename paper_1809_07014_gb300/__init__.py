@@ -81,7 +81,26 @@ class kmer_batch_job(ctypes.Structure):
 
 class kmer_batch_stats(ctypes.Structure):
     _fields_ = [("jobs", ctypes.c_uint32), ("waves", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32),
-                ("jobs_alone", ctypes.c_uint32), ("ms_total", ctypes.c_float)]
+                ("jobs_alone", ctypes.c_uint32), ("fallback_leaves", ctypes.c_uint32), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class kmer_request_info(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class kmer_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("workers", ctypes.c_uint32), ("peak_running", ctypes.c_uint32), ("pending", ctypes.c_uint32),
+                ("running", ctypes.c_uint32), ("pooled", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("bytes_in_use", ctypes.c_uint64), ("budget", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -110,6 +129,14 @@ _SIGNATURES = {
     "kmer_batch_copy_results": (_int, [_vp, _u32, _vp, _vp, _vp, _vp, _u64]),
     "kmer_batch_get_stats": (_int, [_vp, ctypes.POINTER(kmer_batch_stats)]),
     "kmer_batch_destroy": (_int, [_vp]),
+    "kmer_server_create": (_int, [_u64, _u32, ctypes.POINTER(_vp)]),
+    "kmer_server_submit": (_int, [_vp, _vp, ctypes.POINTER(kmer_analysis_params), ctypes.POINTER(_u64)]),
+    "kmer_server_poll": (_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int)]),
+    "kmer_server_wait": (_int, [_vp, _u64, ctypes.POINTER(kmer_result_view), ctypes.POINTER(kmer_request_info)]),
+    "kmer_server_copy_results": (_int, [_vp, _u64, _vp, _vp, _vp, _vp, _u64]),
+    "kmer_server_release": (_int, [_vp, _u64]),
+    "kmer_server_get_stats": (_int, [_vp, ctypes.POINTER(kmer_server_stats)]),
+    "kmer_server_destroy": (_int, [_vp]),
     "kmer_analysis_run_noalloc": (_int, [_vp, _vp, _vp, _u64, ctypes.POINTER(kmer_analysis_params), _vp, _vp, _vp,
                                          _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "kmer_strerror": (ctypes.c_char_p, [_int]),
@@ -264,6 +291,49 @@ def kmer_batch_get_stats(b: int) -> kmer_batch_stats:
 
 def kmer_batch_destroy(b: int) -> None:
     _check(load_library().kmer_batch_destroy(b), "kmer_batch_destroy")
+
+
+def kmer_server_create(memory_budget: int = 0, workers: int = 4) -> int:
+    out = _vp()
+    _check(load_library().kmer_server_create(memory_budget, workers, ctypes.byref(out)), "kmer_server_create")
+    return out.value
+
+
+def kmer_server_submit(srv: int, rs: int, params: kmer_analysis_params) -> int:
+    rid = _u64()
+    _check(load_library().kmer_server_submit(srv, rs, ctypes.byref(params), ctypes.byref(rid)), "kmer_server_submit")
+    return rid.value
+
+
+def kmer_server_poll(srv: int, rid: int) -> bool:
+    d = ctypes.c_int()
+    _check(load_library().kmer_server_poll(srv, rid, ctypes.byref(d)), "kmer_server_poll")
+    return bool(d.value)
+
+
+def kmer_server_wait(srv: int, rid: int) -> tuple[kmer_result_view, kmer_request_info]:
+    v, info = kmer_result_view(), kmer_request_info()
+    _check(load_library().kmer_server_wait(srv, rid, ctypes.byref(v), ctypes.byref(info)), "kmer_server_wait")
+    return v, info
+
+
+def kmer_server_copy_results(srv: int, rid: int, keys: int, count: int, ext: int, cls: int, capacity: int) -> None:
+    _check(load_library().kmer_server_copy_results(srv, rid, keys, count, ext, cls, capacity),
+           "kmer_server_copy_results")
+
+
+def kmer_server_release(srv: int, rid: int) -> None:
+    _check(load_library().kmer_server_release(srv, rid), "kmer_server_release")
+
+
+def kmer_server_get_stats(srv: int) -> kmer_server_stats:
+    st = kmer_server_stats()
+    _check(load_library().kmer_server_get_stats(srv, ctypes.byref(st)), "kmer_server_get_stats")
+    return st
+
+
+def kmer_server_destroy(srv: int) -> None:
+    _check(load_library().kmer_server_destroy(srv), "kmer_server_destroy")
 
 
 def kmer_strerror(code: int) -> str:
@@ -458,6 +528,57 @@ class Batch:
     def close(self):
         if self.handle:
             kmer_batch_destroy(self.handle)
+            self.handle = 0
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop (kmer_server_*): submit(readset, k=..., ...) from any thread,
+    wait(id) for the device view and timestamps, results(id) for a host copy,
+    release(id) when done."""
+
+    def __init__(self, memory_budget: int = 0, workers: int = 4):
+        self.handle = kmer_server_create(memory_budget, workers)
+        self._keep = {}
+
+    def submit(self, rs: ReadSet, k: int, **params) -> int:
+        rid = kmer_server_submit(self.handle, rs.handle, make_params(k, **params))
+        self._keep[rid] = rs
+        return rid
+
+    def done(self, rid: int) -> bool:
+        return kmer_server_poll(self.handle, rid)
+
+    def wait(self, rid: int):
+        v, info = kmer_server_wait(self.handle, rid)
+        return v, info.as_dict()
+
+    def results(self, rid: int) -> Result:
+        v, _ = self.wait(rid)
+        n, W = int(v.n), int(v.words)
+        keys = np.empty((n, W), dtype=np.uint64)
+        count = np.empty(n, dtype=np.uint32)
+        ext = np.empty((n, 8), dtype=np.uint32)
+        cls = np.empty((n, 2), dtype=np.uint8)
+        kmer_server_copy_results(self.handle, rid, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
+        return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def release(self, rid: int):
+        kmer_server_release(self.handle, rid)
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        return kmer_server_get_stats(self.handle).as_dict()
+
+    def close(self):
+        if self.handle:
+            kmer_server_destroy(self.handle)
             self.handle = 0
         self._keep.clear()
 

@@ -70,6 +70,7 @@ struct kmer_batch {
     DevBuf zero;                // per wave: level-1/2 fill counters (largest wave)
     DevBuf misc;                // one Misc per job
     DevBuf fb;                  // fallback lists: 64 entries per job
+    DevBuf hbm;                 // HBM table for leaves recounted after a wave
     std::vector<Misc> host_misc;
     kmer_batch_stats st{};
     bool have_result = false;
@@ -172,7 +173,7 @@ int bind_job(kmer_batch* b, BJob& j, unsigned char* scratch, unsigned char* zero
     d.t_ext = j.p.t_ext;
     d.l2_slack_num = 512;
     const double ratio = j.p.distinct_hint && j.windows
-                             ? std::min(1.0, 2.0 * (double)j.p.distinct_hint / (double)j.windows + 0.05)
+                             ? std::min(1.0, 2.5 * (double)j.p.distinct_hint / (double)j.windows + 0.1)
                              : 1.0;
     d.table_ratio_num = (unsigned)(ratio * 65536.0);
     return KMER_OK;
@@ -286,9 +287,15 @@ int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_bu
         CK(cudaMemGetInfo(&fr, &tot));
         budget = (size_t)(0.6 * (double)fr);
     }
-    // persistent per-job state: outputs, counters, fallback lists
-    size_t persistent = 0;
-    for (auto& j : b->jobs) persistent += j.out_cap * (8ull * j.W + 4 + 32 + 2);
+    // persistent per-job state: outputs, counters, fallback lists.  When the
+    // exact upper bound (windows / min_count survivors) of every job fits in
+    // 40% of the budget it is used, so no job can overflow its output.
+    size_t persistent = 0, exact = 0;
+    for (auto& j : b->jobs) exact += (j.windows / j.p.min_count + 1024) * (8ull * j.W + 4 + 32 + 2);
+    for (auto& j : b->jobs) {
+        if (exact <= budget / 5 * 2) j.out_cap = j.windows / j.p.min_count + 1024;
+        persistent += j.out_cap * (8ull * j.W + 4 + 32 + 2);
+    }
     if (persistent >= budget) return fail(KMER_ERR_OOM, "batch outputs alone need %zu bytes", persistent);
     const size_t scratch_budget = budget - persistent;
     // waves: jobs in the given order, as many as fit; a job larger than the budget runs alone
@@ -370,21 +377,71 @@ int run_alone(kmer_batch* b, BJob& j) {
     return KMER_OK;
 }
 
+// Leaves of job j that the wave's leaf kernel handed to the HBM recount
+// (too many distinct keys or records for a shared-memory table): recounted
+// now, while the wave's scratch still holds their records.  Returns false if
+// the job must instead run alone (output too small for the extra survivors).
+int batch_fallbacks(kmer_batch* b, BJob& j, unsigned idx, const Misc& m, bool* ok) {
+    *ok = false;
+    const unsigned n = m.fb_n;
+    std::vector<unsigned> leaves(n);
+    CK(cudaMemcpyAsync(leaves.data(), b->fb.as<unsigned>() + 64ull * idx, n * 4ull, cudaMemcpyDeviceToHost,
+                       b->stream));
+    std::vector<unsigned long long> fill(n);
+    const unsigned long long* fsrc = j.g.p2 ? j.job.l2_fill : j.job.l1_fill;
+    CK(cudaStreamSynchronize(b->stream));
+    for (unsigned i = 0; i < n; ++i)
+        CK(cudaMemcpyAsync(&fill[i], fsrc + leaves[i], 8, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    unsigned long long extra = 0, max_n = 0;
+    for (unsigned i = 0; i < n; ++i) {
+        extra += fill[i] / j.p.min_count + 1;
+        max_n = std::max(max_n, fill[i]);
+    }
+    if (m.out_n + extra > j.out_cap) return KMER_OK;
+    const size_t eb = hbm_entry_bytes(j.W);
+    TRY(b->hbm.ensure(next_pow2(std::max<unsigned long long>(1024, 2 * max_n)) * eb));
+    for (unsigned i = 0; i < n; ++i) {
+        const unsigned long long c = next_pow2(std::max<unsigned long long>(1024, 2 * fill[i]));
+        CK(cudaMemsetAsync(b->hbm.p, 0, c * eb, b->stream));
+        CK(launch_records_insert(j.job, leaves[i], b->hbm.p, c, b->num_sms, b->stream));
+        CK(launch_hbm_sweep(j.job, b->hbm.p, c, b->num_sms, b->stream));
+    }
+    Misc after{};
+    CK(cudaMemcpyAsync(&after, b->misc.as<Misc>() + idx, sizeof(Misc), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->host_misc[idx] = after;
+    *ok = after.status == 0 && after.stats[0] == after.stats[2];
+    b->st.fallback_leaves += n;
+    return KMER_OK;
+}
+
 int run_batch(kmer_batch* b) {
     const auto t0 = std::chrono::steady_clock::now();
     b->have_result = false;
     b->st.graph_launches = 0;
     b->st.jobs_alone = 0;
+    b->st.fallback_leaves = 0;
     if (b->own_stream) CK(cudaDeviceSynchronize());  // re-packed readsets on other streams are complete
+    const size_t n = b->jobs.size();
+    std::vector<char> good(n, 0);
     for (auto& w : b->waves) {
         CK(cudaGraphLaunch(w.exec, b->stream));
         b->st.graph_launches++;
-    }
-    const size_t n = b->jobs.size();
-    if (n) {
+        // check the wave before the next one reuses its scratch
         CK(cudaMemcpyAsync(b->host_misc.data(), b->misc.p, n * sizeof(Misc), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (unsigned id : w.ids) {
+            const Misc& m = b->host_misc[id];
+            if (m.status == 0 && m.fb_n == 0 && m.stats[0] == m.stats[2]) {
+                good[id] = 1;
+            } else if (m.status == 0 && m.fb_n > 0) {
+                bool ok = false;
+                TRY(batch_fallbacks(b, b->jobs[id], id, m, &ok));
+                good[id] = ok ? 1 : 0;
+            }
+        }
     }
-    CK(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < n; ++i) {
         BJob& j = b->jobs[i];
         j.used_alone = false;
@@ -392,13 +449,12 @@ int run_batch(kmer_batch* b) {
             j.n_out = j.res_windows = j.res_distinct = 0;
             continue;
         }
-        const Misc& m = b->host_misc[i];
-        const bool ok = j.wave >= 0 && m.status == 0 && m.fb_n == 0 && m.stats[0] == m.stats[2];
-        if (ok) {
+        if (good[i]) {
+            const Misc& m = b->host_misc[i];
             j.n_out = m.out_n;
             j.res_windows = m.stats[0];
             j.res_distinct = m.stats[1];
-        } else {  // undersized buffer, fallback leaf or too large for a wave: exact regular path
+        } else {  // undersized buffer, failed wait or too large for a wave: exact regular path
             TRY(run_alone(b, j));
             b->st.jobs_alone++;
         }

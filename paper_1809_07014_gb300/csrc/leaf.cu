@@ -123,8 +123,11 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
     const unsigned long long tail = rec[W - 1];
     const unsigned e5 = (unsigned)(tail & 31ull);
     const unsigned long long ktail = (tail & ~63ull) | kKeyMark;
+    // home group from every in-leaf bit of z (for short keys the top bits of the
+    // low word are partition bits, constant within a leaf): multiplicative hash
     const unsigned long long zl = tail >> 6;
-    unsigned g = (unsigned)(((unsigned long long)(unsigned)(zl ^ (zl >> 32)) * ngroups) >> 32);
+    const unsigned hsh = (unsigned)((zl * 0x9E3779B97F4A7C15ull) >> 32);
+    unsigned g = (unsigned)(((unsigned long long)hsh * ngroups) >> 32);
     int found = -1;
     for (unsigned probe = 0; probe < kMaxGroupProbes && found < 0; ++probe) {
         unsigned long long* grp = t.tail + 4 * g;

@@ -1,0 +1,89 @@
+"""Serving: requests that arrive while others run are admitted as memory
+frees up and overlap on the device; every result is the same alone and in
+the mix (exact: all integer)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1809_07014_gb300 as pkg
+from tests.test_batch_gpu import same_result
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def readsets():
+    import torch
+    assert torch.cuda.is_available()
+    out = []
+    for i, n in enumerate([40000, 3000, 15000, 800, 25000, 6000]):
+        s = synth.generate(synth.metagenome_sample(20 + i, n * 150, n_genomes=4 + i).scaled(
+            n, genome_len_min=30_000, genome_len_max=90_000))
+        out.append(pkg.ReadSet(s.bases, s.quals, s.offsets))
+    return out
+
+
+def alone(rs, k):
+    ka = pkg.KmerAnalysis(k)
+    ka.submit(rs)
+    r = ka.results()
+    ka.close()
+    return r
+
+
+REQUESTS = [(0, 21), (1, 33), (2, 55), (3, 77), (4, 99), (5, 21), (0, 33), (2, 21), (4, 55), (1, 21), (0, 21)]
+
+
+def test_results_same_alone_and_in_the_mix(readsets):
+    want = {i: alone(readsets[r], k) for i, (r, k) in enumerate(REQUESTS)}
+    srv = pkg.Server(workers=4)
+    ids = {}
+
+    def client(part):
+        for i in part:  # staggered arrivals from several threads
+            r, k = REQUESTS[i]
+            ids[i] = srv.submit(readsets[r], k)
+            time.sleep(0.002 * (i % 3))
+
+    threads = [threading.Thread(target=client, args=(list(range(j, len(REQUESTS), 3)),)) for j in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    infos = {}
+    for i, rid in ids.items():
+        got = srv.results(rid)
+        same_result(got, want[i])
+        infos[i] = srv.wait(rid)[1]
+        assert infos[i]["status"] == 0 and infos[i]["t_done_ms"] >= infos[i]["t_start_ms"] >= infos[i]["t_submit_ms"]
+        srv.release(rid)
+    st = srv.stats()
+    assert st["completed"] == len(REQUESTS) and st["failed"] == 0
+    assert st["peak_running"] >= 2, "requests never overlapped"
+    srv.close()
+
+
+def test_admission_by_footprint_queues_and_stays_exact(readsets):
+    """A budget that holds about one large request at a time: later requests wait
+    for releases (pending) and reuse pooled analyses; results stay exact."""
+    srv = pkg.Server(memory_budget=600 << 20, workers=3)
+    reqs = [(0, 21), (4, 21), (0, 21), (2, 33), (4, 21)]
+    ids = [srv.submit(readsets[r], k) for r, k in reqs]
+    assert srv.stats()["pending"] >= 1
+    for rid, (r, k) in zip(ids, reqs):
+        same_result(srv.results(rid), alone(readsets[r], k))
+        srv.release(rid)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    srv.close()
+
+
+def test_bad_request_rejected(readsets):
+    srv = pkg.Server(workers=1)
+    with pytest.raises(pkg.KmerError) as e:
+        srv.submit(readsets[0], 22)
+    assert e.value.code == pkg.KMER_ERR_INVALID_ARG
+    srv.close()
