@@ -130,6 +130,32 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def barrier() -> None:
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def reduce_over_ranks(seconds: float, windows: int, device) -> tuple[float, int]:
+    """Whole-job figures: the slowest rank's timed region and the windows all
+    ranks analysed (each rank runs its own sample; nothing else is exchanged)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return seconds, windows
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([windows], device=device, dtype=torch.int64)
+    dist.all_reduce(w)
+    return float(t.item()), int(w.item())
+
+
 def workload(rank: int, n_reads: int):
     import synth
     r = synth.METAGENOME_2G
@@ -165,7 +191,7 @@ def config_of(args, recipe, n_bases):
 
 # ------------------------------------------------------------- reference arm
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return  # the oracle runs on rank 0 only
     import synth
@@ -198,9 +224,7 @@ def run_ours(args):
     import synth
     import paper_1809_07014_gb300 as pkg
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -234,8 +258,7 @@ def run_ours(args):
     launches = 0
     clocks = Clocks(local)
     clocks.start()
-    if world > 1:
-        dist.barrier()
+    barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -249,19 +272,10 @@ def run_ours(args):
         windows += int(v.windows)
     e1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    ms_max = ms
-    tot_windows = windows
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        w = torch.tensor([windows], device=dev, dtype=torch.float64)
-        dist.all_reduce(w)
-        tot_windows = int(w.item())
-    value = tot_windows / (ms_max / 1e3)
+    barrier()
+    sec_max, tot_windows = reduce_over_ranks(e0.elapsed_time(e1) / 1e3, windows, dev)
+    ms_max = 1e3 * sec_max
+    value = tot_windows / sec_max
     st = ka.stats()
     n_surv = int(v.n)
     W = int(v.words)
@@ -321,21 +335,16 @@ def run_ours(args):
             return vv
         vv = e2e_step()
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier()
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
             vv = e2e_step()
             d2h += int(vv.n) * (8 * W + 4 + 32 + 2)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt, e2e_windows = reduce_over_ranks(time.perf_counter() - t0, windows, dev)
         h2d = 2 * n_bases + 8 * (n_reads + 1)
-        line["e2e"] = {"value": tot_windows / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        line["e2e"] = {"value": e2e_windows / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h // args.steps, "ms_per_step": 1e3 * dt / args.steps}
         rset_h.close()
     line["clocks"] = clocks.stop()
