@@ -678,16 +678,21 @@ int do_query(kmer_analysis* h) {
                 CK(cudaMemGetInfo(&fr, &tot));
                 budget = (size_t)(0.85 * (double)(fr + h->device_bytes()));
             }
-            const Plan pl = make_plan(h, windows, budget, cap_max);
+            // output sized from the previous query or a fraction of the windows, at most
+            // 35 % of the budget on a first query; grown on demand
+            const unsigned long long out_bytes_per = 8ull * W + 4 + 32 + 2;
+            const unsigned long long bound = windows / h->p.min_count + 1024;
+            unsigned long long want = h->out_hint ? h->out_hint + h->out_hint / 16 + 4096 : windows / 4 + 4096;
+            if (!h->out_hint) want = std::min<unsigned long long>(want, 0.35 * (double)budget / out_bytes_per + 4096);
+            TRY(ensure_output(h, std::min(bound, want), 0));
+            // the records of a pass get what the output leaves of the budget
+            const size_t out_bytes = (size_t)(h->out_cap * out_bytes_per);
+            const Plan pl = make_plan(h, windows, budget > 2 * out_bytes ? budget - out_bytes : budget / 2, cap_max);
             h->st.pass_bits = pl.g.ps;
             h->st.l1_bits = pl.g.p1;
             h->st.l2_bits = pl.g.p2;
             h->st.leaf_table_slots = cap_max;
             h->st.passes = pl.passes;
-            // output sized from the previous query or a fraction of the windows; grown on demand
-            const unsigned long long bound = windows / h->p.min_count + 1024;
-            unsigned long long want = h->out_hint ? h->out_hint + h->out_hint / 16 + 4096 : windows / 4 + 4096;
-            TRY(ensure_output(h, std::min(bound, want), 0));
             for (unsigned pass = 0; pass < pl.passes; ++pass) TRY(run_pass(h, pl, pass, cap_max));
         }
     }

@@ -105,50 +105,77 @@ __global__ void __launch_bounds__(kStageThreads) job_tiles_kernel(const Job* __r
     if (threadIdx.x == 0) job_tile_off[n_jobs] = s_run;
 }
 
+// Where one level-2 tile's records are: its analysis, bucket and record range.
+struct RepartTile {
+    unsigned ji, bucket, cnt;
+    const unsigned long long* src;
+};
+
+__device__ __forceinline__ RepartTile repart_tile_at(const Job* __restrict__ jobs,
+                                                     const unsigned long long* __restrict__ job_tile_off,
+                                                     const unsigned n_jobs, const unsigned long long gt,
+                                                     const unsigned S) {
+    RepartTile rt;
+    rt.ji = job_of(job_tile_off, n_jobs, gt);
+    const Job& j = jobs[rt.ji];
+    const unsigned long long tile = gt - job_tile_off[rt.ji];
+    // bucket of this tile: last b with tile_prefix[b] <= tile
+    unsigned lo = 0, hi = (1u << j.g.p1) - 1;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi + 1) >> 1;
+        if (j.tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    rt.bucket = lo;
+    const unsigned long long f = j.l1_fill[lo], c = j.l1_cap[lo];
+    const unsigned long long n = f < c ? f : c;
+    const unsigned long long begin = (tile - j.tile_prefix[lo]) * S;
+    rt.cnt = (unsigned)(n - begin < S ? n - begin : S);
+    rt.src = j.l1_rec + (j.l1_start[lo] + begin) * j.g.W;
+    return rt;
+}
+
+// Persistent CTAs over the level-2 tiles of every analysis.  A tile's records
+// are requested (into registers) before the previous tile is flushed, so the
+// loads overlap the flush.  Shared memory is laid out for `pmax` leaves per
+// bucket, the largest fan-out of the launch.
 template <int W, unsigned MAXPER>
 __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __restrict__ jobs,
                                                                  const unsigned long long* __restrict__ job_tile_off,
-                                                                 const unsigned n_jobs) {
+                                                                 const unsigned n_jobs, const unsigned pmax) {
     constexpr unsigned S = RepartShape<W>::S;
+    constexpr unsigned U = S / kStageThreads;
     extern __shared__ __align__(16) unsigned char smem[];
+    const StageBufs b = carve_stage(smem, W, S, pmax);
+    for (unsigned d = threadIdx.x; d < pmax; d += kStageThreads) b.hist[d] = 0;
     const unsigned long long all = job_tile_off[n_jobs];
-    for (unsigned long long gt = blockIdx.x; gt < all; gt += gridDim.x) {
-        const unsigned ji = job_of(job_tile_off, n_jobs, gt);
-        const Job& j = jobs[ji];
-        const unsigned long long tile = gt - job_tile_off[ji];
-        const unsigned P1 = 1u << j.g.p1, P2 = 1u << j.g.p2;
-        StageBufs b = carve_stage(smem, W, S, P2);
-        for (unsigned d = threadIdx.x; d < P2; d += kStageThreads) b.hist[d] = 0;
-        __syncthreads();
-        const unsigned zb = j.g.zl_bits();
-        // bucket of this tile: last b with tile_prefix[b] <= tile
-        unsigned lo = 0, hi = P1 - 1;
-        while (lo < hi) {
-            const unsigned mid = (lo + hi + 1) >> 1;
-            if (j.tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
-        }
-        const unsigned bucket = lo;
-        const unsigned long long f = j.l1_fill[bucket], c = j.l1_cap[bucket];
-        const unsigned long long n = f < c ? f : c;
-        const unsigned long long begin = (tile - j.tile_prefix[bucket]) * S;
-        const unsigned cnt = (unsigned)(n - begin < S ? n - begin : S);
-        const unsigned long long* src = j.l1_rec + (j.l1_start[bucket] + begin) * W;
-        // all of this thread's records of the tile are requested before any is used
-        constexpr unsigned U = S / kStageThreads;
-        unsigned long long rec[U][W];
+    unsigned long long gt = blockIdx.x;
+    unsigned long long rec[U][W];
+    RepartTile rt{};
+    auto load = [&](const RepartTile& x) {
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
             const unsigned e = u * kStageThreads + threadIdx.x;
 #pragma unroll
-            for (int w = 0; w < W; ++w) rec[u][w] = e < cnt ? __ldcs(src + (size_t)e * W + w) : 0ull;
+            for (int w = 0; w < W; ++w) rec[u][w] = e < x.cnt ? __ldcs(x.src + (size_t)e * W + w) : 0ull;
         }
+    };
+    if (gt < all) {
+        rt = repart_tile_at(jobs, job_tile_off, n_jobs, gt, S);
+        load(rt);
+    }
+    __syncthreads();
+    while (gt < all) {
+        const Job& j = jobs[rt.ji];
+        const unsigned P2 = 1u << j.g.p2;
+        const unsigned zb = j.g.zl_bits();
+        const unsigned shift = zb - j.g.p2;
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
             const unsigned e = u * kStageThreads + threadIdx.x;
             unsigned m = 0xFFFFFFFFu;
-            if (e < cnt) {
+            if (e < rt.cnt) {
                 const unsigned long long zl = rec[u][W - 1] >> 6;
-                const unsigned sub = (unsigned)(zl >> (zb - j.g.p2)) & (P2 - 1u);
+                const unsigned sub = (unsigned)(zl >> shift) & (P2 - 1u);
                 const unsigned rank = atomicAdd(&b.hist[sub], 1u);
 #pragma unroll
                 for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[u][w];
@@ -156,8 +183,17 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __r
             }
             b.meta[e] = m;
         }
-        L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[bucket], j.l2_leafcap[bucket], bucket << j.g.p2};
+        // the next tile's loads are in flight during this tile's flush
+        const unsigned long long ngt = gt + gridDim.x;
+        RepartTile nrt{};
+        if (ngt < all) {
+            nrt = repart_tile_at(jobs, job_tile_off, n_jobs, ngt, S);
+            load(nrt);
+        }
+        L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[rt.bucket], j.l2_leafcap[rt.bucket], rt.bucket << j.g.p2};
         flush_stage<W, MAXPER>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
+        gt = ngt;
+        rt = nrt;
     }
 }
 
@@ -179,7 +215,7 @@ static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* j
     cudaError_t e =
         cudaFuncSetAttribute(repart_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(jobs, job_tile_off, n_jobs);
+    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
     return cudaGetLastError();
 }
 

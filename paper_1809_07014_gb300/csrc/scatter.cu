@@ -11,7 +11,7 @@ namespace kmer {
 
 template <int W>
 struct ScatterShape {
-    static constexpr unsigned R = W == 1 ? 8 : (W == 2 ? 4 : 2);  // read positions per round
+    static constexpr unsigned R = W == 1 ? 16 : (W == 2 ? 8 : 4);  // read positions per round
     static constexpr unsigned S = R * kStageThreads;                 // staged records per round
 };
 

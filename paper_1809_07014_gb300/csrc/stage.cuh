@@ -68,41 +68,43 @@ __device__ inline unsigned long long block_scan_u64(unsigned long long v, unsign
 }
 
 struct StageBufs {
-    unsigned long long* stage;   // S * W
-    unsigned long long* sorted;  // S * W
+    unsigned long long* stage;   // S * W: records in arrival order
     unsigned long long* wbase;   // P: record index of sorted position 0 of destination d
     unsigned long long* limit;   // P: first record index past destination d
     unsigned* meta;              // S
     unsigned* hist;              // P
     unsigned* lbase;             // P
-    unsigned short* sorted_b;    // S
+    unsigned short* order;       // S: staged index of each sorted position
     unsigned* warp_tmp;          // 8
 };
 
 __host__ __device__ inline size_t stage_smem_bytes(unsigned W, unsigned S, unsigned P) {
-    return (size_t)S * W * 8 * 2 + (size_t)P * 16 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
+    return (size_t)S * W * 8 + (size_t)P * 16 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
 }
 
 __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigned S, unsigned P) {
     StageBufs b;
     b.stage = reinterpret_cast<unsigned long long*>(base);
-    b.sorted = b.stage + (size_t)S * W;
-    b.wbase = b.sorted + (size_t)S * W;
+    b.wbase = b.stage + (size_t)S * W;
     b.limit = b.wbase + P;
     b.meta = reinterpret_cast<unsigned*>(b.limit + P);
     b.hist = b.meta + S;
     b.lbase = b.hist + P;
-    b.sorted_b = reinterpret_cast<unsigned short*>(b.lbase + P);
-    b.warp_tmp = reinterpret_cast<unsigned*>(b.sorted_b + S + 8);  // 16-byte slack keeps it 4-aligned
+    b.order = reinterpret_cast<unsigned short*>(b.lbase + P);
+    b.warp_tmp = reinterpret_cast<unsigned*>(b.order + S + 8);  // 16-byte slack keeps it 4-aligned
     return b;
 }
 
 // Flush one round.  meta[e] = (dest << 16) | rank for a staged record e, or
-// 0xFFFFFFFF; hist[d] = records staged for destination d.  Dest supplies
-// reserve(d, n) -> first slot index within d, start(d) -> record index of
-// slot 0 of d, cap(d) -> slots of d.  Records past cap are dropped and
-// reported through `status` (the host then retries with exact capacities).
-// hist is left zeroed for the next round.
+// 0xFFFFFFFF; hist[d] = records staged for destination d (S <= 65536).  Dest
+// supplies reserve(d, n) -> first slot index within d, start(d) -> record
+// index of slot 0 of d, cap(d) -> slots of d.  Records past cap are dropped
+// and reported through `status` (the host then retries with exact
+// capacities).  hist is left zeroed for the next round.
+//
+// The records are not moved inside shared memory: a 16-bit index per sorted
+// position says which staged record goes there, and consecutive threads
+// write consecutive positions, i.e. contiguous runs per destination.
 template <int W, unsigned MAXPER, class Dest>
 __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
                             unsigned* status, unsigned overflow_bit) {
@@ -134,22 +136,17 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     __syncthreads();
     for (unsigned e = threadIdx.x; e < S; e += kStageThreads) {
         const unsigned m = b.meta[e];
-        if (m != 0xFFFFFFFFu) {
-            const unsigned d = m >> 16;
-            const unsigned pos = b.lbase[d] + (m & 0xFFFFu);
-#pragma unroll
-            for (int w = 0; w < W; ++w) b.sorted[(size_t)pos * W + w] = b.stage[(size_t)e * W + w];
-            b.sorted_b[pos] = (unsigned short)d;
-        }
+        if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (unsigned short)e;
     }
     __syncthreads();
     bool over = false;
     for (unsigned pos = threadIdx.x; pos < total; pos += kStageThreads) {
-        const unsigned d = b.sorted_b[pos];
+        const unsigned e = b.order[pos];
+        const unsigned d = b.meta[e] >> 16;
         const unsigned long long g = b.wbase[d] + pos;
         if (g < b.limit[d]) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) out_rec[g * W + w] = b.sorted[(size_t)pos * W + w];
+            for (int w = 0; w < W; ++w) out_rec[g * W + w] = b.stage[(size_t)e * W + w];
         } else {
             over = true;
         }
