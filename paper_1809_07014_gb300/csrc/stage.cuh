@@ -70,28 +70,28 @@ __device__ inline unsigned long long block_scan_u64(unsigned long long v, unsign
 struct StageBufs {
     unsigned long long* stage;   // S * W: records in arrival order
     unsigned long long* wbase;   // P: record index of sorted position 0 of destination d
-    unsigned long long* limit;   // P: first record index past destination d
+    unsigned* ok_end;            // P: first sorted position of destination d past its capacity
     unsigned* meta;              // S
     unsigned* hist;              // P
     unsigned* lbase;             // P
-    unsigned short* order;       // S: staged index of each sorted position
+    unsigned* order;             // S: (destination << 16) | staged index, per sorted position
     unsigned* warp_tmp;          // 8
 };
 
 __host__ __device__ inline size_t stage_smem_bytes(unsigned W, unsigned S, unsigned P) {
-    return (size_t)S * W * 8 + (size_t)P * 16 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 2 + 64;
+    return (size_t)S * W * 8 + (size_t)P * 8 + (size_t)P * 4 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 4 + 64;
 }
 
 __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigned S, unsigned P) {
     StageBufs b;
     b.stage = reinterpret_cast<unsigned long long*>(base);
     b.wbase = b.stage + (size_t)S * W;
-    b.limit = b.wbase + P;
-    b.meta = reinterpret_cast<unsigned*>(b.limit + P);
+    b.ok_end = reinterpret_cast<unsigned*>(b.wbase + P);
+    b.meta = b.ok_end + P;
     b.hist = b.meta + S;
     b.lbase = b.hist + P;
-    b.order = reinterpret_cast<unsigned short*>(b.lbase + P);
-    b.warp_tmp = reinterpret_cast<unsigned*>(b.order + S + 8);  // 16-byte slack keeps it 4-aligned
+    b.order = b.lbase + P;
+    b.warp_tmp = b.order + S;
     return b;
 }
 
@@ -102,9 +102,10 @@ __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigne
 // and reported through `status` (the host then retries with exact
 // capacities).  hist is left zeroed for the next round.
 //
-// The records are not moved inside shared memory: a 16-bit index per sorted
-// position says which staged record goes there, and consecutive threads
-// write consecutive positions, i.e. contiguous runs per destination.
+// The records are not moved inside shared memory: a word per sorted position
+// says which staged record goes there and to which destination, and
+// consecutive threads write consecutive positions, i.e. contiguous runs per
+// destination.
 template <int W, unsigned MAXPER, class Dest>
 __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
                             unsigned* status, unsigned overflow_bit) {
@@ -119,6 +120,7 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     unsigned run = block_scan_u32(mine, b.warp_tmp, &total);
     // reservations of this thread's destinations are independent: unrolled so
     // that all of them are in flight together
+    bool over = false;
 #pragma unroll
     for (unsigned i = 0; i < MAXPER; ++i) {
         const unsigned d = d0 + i;
@@ -126,9 +128,12 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
             const unsigned h = b.hist[d];
             b.lbase[d] = run;
             if (h) {
-                const unsigned long long st = dest.start(d);
-                b.wbase[d] = st + dest.reserve(d, h) - run;
-                b.limit[d] = st + dest.cap(d);
+                const unsigned long long first = dest.reserve(d, h), cap = dest.cap(d);
+                b.wbase[d] = dest.start(d) + first - run;
+                // positions of d that still fit: [run, run + min(h, cap - first))
+                const unsigned long long room = first < cap ? cap - first : 0ull;
+                b.ok_end[d] = run + (unsigned)(room < h ? room : h);
+                over = over || room < h;
             }
             run += h;
         }
@@ -136,19 +141,16 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     __syncthreads();
     for (unsigned e = threadIdx.x; e < S; e += kStageThreads) {
         const unsigned m = b.meta[e];
-        if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (unsigned short)e;
+        if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (m & 0xFFFF0000u) | e;
     }
     __syncthreads();
-    bool over = false;
     for (unsigned pos = threadIdx.x; pos < total; pos += kStageThreads) {
-        const unsigned e = b.order[pos];
-        const unsigned d = b.meta[e] >> 16;
-        const unsigned long long g = b.wbase[d] + pos;
-        if (g < b.limit[d]) {
+        const unsigned o = b.order[pos];
+        const unsigned d = o >> 16, e = o & 0xFFFFu;
+        if (pos < b.ok_end[d]) {
+            const unsigned long long g = b.wbase[d] + pos;
 #pragma unroll
             for (int w = 0; w < W; ++w) out_rec[g * W + w] = b.stage[(size_t)e * W + w];
-        } else {
-            over = true;
         }
     }
     for (unsigned d = threadIdx.x; d < P; d += kStageThreads) b.hist[d] = 0;
