@@ -130,6 +130,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def hash_form_bytes_per_window(k: int, read_len: int, windows: int, distinct: int, survivors: int) -> float:
+    """Algorithmic DRAM bytes per window of k-mer analysis in its hash-table
+    form, the fixed denominator for every variant: the packed input, one
+    table sector read and write-back per window, the table sweep and the
+    survivors' output."""
+    W = (2 * k + 63) // 64
+    inp = 0.5 * read_len / max(1, read_len - k + 1)
+    table = 64.0 if W == 1 else 96.0
+    sweep = distinct * (8 * W + 4 + 16) / max(1, windows)
+    out = survivors * (8 * W + 4 + 32 + 2) / max(1, windows)
+    return inp + table + sweep + out
+
+
 def rank_env() -> tuple[int, int, int]:
     """(world size, rank, local rank) from the launcher's environment."""
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
@@ -307,6 +320,12 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": b, "ms_per_launch": round(ms_l, 4),
                 "traffic": kernel_traffic(dom, src),
                 "stages_ms_per_step": {k[3:]: round(acc[k] / args.steps, 4) for k in stage_keys if k.startswith("ms_")}}
+    # whole-path HBM fraction against the hash form's bytes per window
+    bpw = hash_form_bytes_per_window(args.k, 150, int(st["windows"]), int(st["distinct"]), n_surv)
+    per_gpu = value / world
+    roofline["path_hbm_fraction"] = {"bytes_per_window": round(bpw, 2), "achieved": round(per_gpu * bpw / 1e9, 1),
+                                     "frac": round(per_gpu * bpw / 1e9 / peak, 4),
+                                     "note": "windows/s per GPU x hash-form bytes per window / measured peak"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

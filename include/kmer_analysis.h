@@ -221,8 +221,10 @@ int kmer_analysis_destroy(kmer_analysis_t *h);
  * grouped into waves whose scratch fits the memory budget; each wave is
  * captured once as a CUDA graph in which every stage is one launch over all
  * jobs of a key width, and kmer_batch_run replays the graphs.  A job whose
- * buffers turn out too small (or that is too large for any wave) is re-run
- * alone through the regular path, so results are always exact. */
+ * output or leaf layout turns out too small is repaired inside its wave (the
+ * stages after the scatter re-run for that job); a job whose level-1 buckets
+ * overflow, or that is too large for any wave, is re-run alone through the
+ * regular path.  Results are always exact. */
 typedef struct kmer_batch kmer_batch_t;
 
 typedef struct {
@@ -238,6 +240,11 @@ typedef struct {
     uint32_t jobs_alone;      /* jobs of the last run that went through the regular path */
     uint32_t fallback_leaves; /* leaves of the last run recounted in an HBM table after their wave */
     float ms_total;           /* wall time of the last run, host clock */
+    uint32_t jobs_repaired;   /* jobs of the last run whose output, fallback list or level-2 layout was grown
+                                 inside their wave, the later stages re-run for that job only */
+    uint32_t alone_level1;    /* jobs_alone because a level-1 bucket overflowed */
+    uint32_t alone_other;     /* jobs_alone for another reason (too large for a wave, a failed wait) */
+    uint32_t reserved;
 } kmer_batch_stats;
 
 /* Plans the jobs, allocates every buffer (memory_budget bytes of device

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -36,6 +37,74 @@ int fail(int code, const char* fmt, ...) {
 }
 
 const char* last_error_message() { return g_err.c_str(); }
+
+thread_local cudaStream_t tl_alloc_stream = nullptr;
+
+void prepare_pool(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        unsigned long long keep = ~0ull;  // freed memory stays in the pool for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(device);
+}
+
+size_t free_device_bytes() {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int dev = 0;
+    cudaMemPool_t pool;
+    unsigned long long reserved = 0, used = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+        fr += (size_t)(reserved - used);
+    cudaGetLastError();
+    return fr;
+}
+
+namespace {
+struct PinnedMiscPool {
+    std::mutex mu;
+    std::vector<Misc*> free_list;
+};
+PinnedMiscPool& pinned_pool() {
+    static PinnedMiscPool* pool = new PinnedMiscPool;  // lives for the whole process
+    return *pool;
+}
+}  // namespace
+
+Misc* pinned_misc_get() {
+    PinnedMiscPool& pool = pinned_pool();
+    std::lock_guard<std::mutex> lk(pool.mu);
+    if (pool.free_list.empty()) {
+        constexpr int kChunk = 64;  // Misc blocks per pinned allocation (never returned)
+        Misc* chunk = nullptr;
+        if (cudaMallocHost((void**)&chunk, kChunk * sizeof(Misc)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = kChunk - 1; i >= 0; --i) pool.free_list.push_back(chunk + i);
+    }
+    Misc* m = pool.free_list.back();
+    pool.free_list.pop_back();
+    return m;
+}
+
+void pinned_misc_put(Misc* m) {
+    if (!m) return;
+    PinnedMiscPool& pool = pinned_pool();
+    std::lock_guard<std::mutex> lk(pool.mu);
+    pool.free_list.push_back(m);
+}
 
 Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
                        unsigned cap_max, unsigned leaf_bits, unsigned l1_bits) {
@@ -213,10 +282,16 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
     return KMER_OK;
 }
 
+// The caller has made sure no stream still reads the readset; its buffers
+// are freed in the order of the legacy stream, which always exists (the
+// streams they were packed on may be gone).
 void destroy_readset(kmer_readset* rs) {
     DevBuf* bs[] = {&rs->blocks, &rs->blk_off, &rs->offsets, &rs->tmp_bases, &rs->tmp_quals,
                     &rs->nblk, &rs->scratch, &rs->stats};
-    for (auto* b : bs) b->release();
+    for (auto* b : bs) {
+        b->s = nullptr;
+        b->release();
+    }
     delete rs;
 }
 
@@ -237,10 +312,14 @@ int make_readset(const char* bases, const uint8_t* quals, const uint64_t* offset
     auto* rs = new (std::nothrow) kmer_readset;
     if (!rs) return fail(KMER_ERR_OOM, "host allocation failed");
     rs->device = dev;
+    prepare_pool(dev);
+    StreamScope scope(s);
     rs->qual_offset = qual_offset;
     rs->qual_threshold = qual_threshold;
     int rc = pack_readset(rs, bases, quals, offsets, n_reads, where, s);
     if (rc != KMER_OK) {
+        cudaStreamSynchronize(s);  // nothing may still use the buffers
+        cudaGetLastError();
         destroy_readset(rs);
         return rc;
     }
@@ -673,11 +752,7 @@ int do_query(kmer_analysis* h) {
             const unsigned W = h->W();
             const unsigned cap_max = leaf_table_cap(W, h->leaf_smem_budget);
             size_t budget = h->p.memory_budget;
-            if (!budget) {
-                size_t fr = 0, tot = 0;
-                CK(cudaMemGetInfo(&fr, &tot));
-                budget = (size_t)(0.85 * (double)(fr + h->device_bytes()));
-            }
+            if (!budget) budget = (size_t)(0.85 * (double)(free_device_bytes() + h->device_bytes()));
             // output sized from the previous query or a fraction of the windows, at most
             // 35 % of the budget on a first query; grown on demand
             const unsigned long long out_bytes_per = 8ull * W + 4 + 32 + 2;
@@ -755,6 +830,7 @@ int kmer_readset_pack(kmer_readset_t* rs, const char* bases, const uint8_t* qual
     if (n_reads && (!bases || !quals || !offsets))
         return fail(KMER_ERR_INVALID_ARG, "bases, quals and offsets must be non-NULL when n_reads > 0");
     DeviceGuard dg(rs->device);
+    StreamScope scope(static_cast<cudaStream_t>(cuda_stream));
     return pack_readset(rs, bases, quals, offsets, n_reads, where, static_cast<cudaStream_t>(cuda_stream));
 }
 
@@ -774,6 +850,9 @@ int kmer_readset_info(const kmer_readset_t* rs, uint64_t* n_reads, uint64_t* n_b
 int kmer_readset_destroy(kmer_readset_t* rs) {
     if (!rs) return KMER_OK;
     DeviceGuard dg(rs->device);
+    // analyses on any stream may still read the packed reads
+    cudaDeviceSynchronize();
+    cudaGetLastError();
     destroy_readset(rs);
     return KMER_OK;
 }
@@ -803,8 +882,11 @@ int kmer_analysis_create(const kmer_analysis_params* p, void* cuda_stream, kmer_
     h->num_sms = sms;
     // two leaf CTAs per SM: half the SM's shared memory minus the per-block reserve and statics
     h->leaf_smem_budget = std::min<size_t>((size_t)smem_optin, (size_t)smem_sm / 2 - 1024 - 256);
-    if (h->misc.ensure(sizeof(Misc)) != KMER_OK || cudaMallocHost((void**)&h->host_misc, sizeof(Misc)) != cudaSuccess) {
-        cudaGetLastError();
+    prepare_pool(dev);
+    StreamScope scope(h->stream);
+    h->host_misc = pinned_misc_get();
+    if (!h->host_misc || h->misc.ensure(sizeof(Misc)) != KMER_OK) {
+        pinned_misc_put(h->host_misc);
         h->misc.release();
         delete h;
         return fail(KMER_ERR_OOM, "cannot allocate counters");
@@ -828,6 +910,7 @@ int kmer_analysis_submit_raw(kmer_analysis_t* h, const char* bases, const uint8_
                              uint64_t n_reads, int where) {
     if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
     DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
     kmer_readset* rs = nullptr;
     TRY(make_readset(bases, quals, offsets, n_reads, h->p.qual_offset, h->p.qual_threshold, where, h->stream, &rs));
     h->owned.push_back(rs);
@@ -839,6 +922,7 @@ int kmer_analysis_submit_raw(kmer_analysis_t* h, const char* bases, const uint8_
 int kmer_analysis_query(kmer_analysis_t* h, kmer_result_view* out) {
     if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
     DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
     std::memset(out, 0, sizeof *out);
     int rc = do_query(h);
     if (rc != KMER_OK) {
@@ -885,6 +969,7 @@ int kmer_analysis_get_stats(const kmer_analysis_t* h, kmer_analysis_stats* out) 
 int kmer_analysis_reset(kmer_analysis_t* h) {
     if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
     DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
     h->submitted.clear();
     for (kmer_readset* rs : h->owned) destroy_readset(rs);
     h->owned.clear();
@@ -896,6 +981,7 @@ int kmer_analysis_reset(kmer_analysis_t* h) {
 int kmer_analysis_destroy(kmer_analysis_t* h) {
     if (!h) return KMER_OK;
     DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     kmer_analysis_reset(h);
@@ -903,7 +989,7 @@ int kmer_analysis_destroy(kmer_analysis_t* h) {
                     &h->l2_fill, &h->l2_leaf_start, &h->tile_prefix, &h->out_keys, &h->out_count, &h->out_ext,
                     &h->out_cls, &h->fb_list, &h->hbm, &h->misc};
     for (auto* b : bs) b->release();
-    if (h->host_misc) cudaFreeHost(h->host_misc);
+    pinned_misc_put(h->host_misc);
     for (int i = 0; i < kmer_analysis::STG_N; ++i) {
         if (h->ev_b[i]) cudaEventDestroy(h->ev_b[i]);
         if (h->ev_e[i]) cudaEventDestroy(h->ev_e[i]);

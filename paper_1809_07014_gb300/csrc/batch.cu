@@ -8,9 +8,15 @@
 // memory budget; a wave is captured once as a graph (zero the counters,
 // scatter, plan level 2, repartition, count/classify/compact) and replayed
 // by every run.  Buffers are sized ahead from each job's exact window count
-// and its expected distinct / surviving k-mers; a job whose device status
-// reports any undersized buffer, fallback leaf or failed wait is re-run
-// alone through the regular analysis, which grows buffers until exact.
+// and its expected distinct / surviving k-mers.  After a wave, while its
+// scratch still holds the records, a job whose output or level-2 layout was
+// too small is repaired in place: its output (or fallback list) is grown, or
+// its leaves get an exact layout from the counts the repartition took, and
+// the later stages are re-run for that job alone; the repaired descriptor is
+// kept for later runs.  Leaves that did not fit an on-chip table are
+// recounted in an HBM table.  Only a job whose level-1 buckets overflowed,
+// or that is too large for any wave, runs alone through the regular
+// analysis.
 #include <chrono>
 #include <memory>
 
@@ -35,6 +41,9 @@ struct BJob {
     int wave = -1;            // -1: runs alone through the regular path
     unsigned slot = 0;        // index in its wave's job array
     DevBuf out_keys, out_count, out_ext, out_cls;
+    DevBuf fb;                // fallback leaf list
+    unsigned fb_cap = 64;
+    DevBuf l2_exact;          // exact level-2 layout, once a leaf overflowed its uniform capacity
     DevBuf consts;            // level-1 bucket starts and capacities (fixed for the batch's life)
     Job job{};                // device descriptor (pointers filled per wave)
     kmer_analysis_t* alone = nullptr;  // regular analysis used for this job, if any
@@ -69,8 +78,8 @@ struct kmer_batch {
     DevBuf scratch;             // shared by the waves (they run one after the other)
     DevBuf zero;                // per wave: level-1/2 fill counters (largest wave)
     DevBuf misc;                // one Misc per job
-    DevBuf fb;                  // fallback lists: 64 entries per job
     DevBuf hbm;                 // HBM table for leaves recounted after a wave
+    DevBuf one_maps;            // work maps of a single-job re-run: leaf_off[2], job_tile_off[2]
     std::vector<Misc> host_misc;
     kmer_batch_stats st{};
     bool have_result = false;
@@ -162,9 +171,10 @@ int bind_job(kmer_batch* b, BJob& j, unsigned char* scratch, unsigned char* zero
     d.out_n = &m->out_n;
     d.status = &m->status;
     d.stats = m->stats;
-    d.fb_list = b->fb.as<unsigned>() + 64ull * idx;
+    TRY(j.fb.ensure(j.fb_cap * 4ull));
+    d.fb_list = j.fb.as<unsigned>();
     d.fb_n = &m->fb_n;
-    d.fb_cap = 64;
+    d.fb_cap = j.fb_cap;
     d.min_count = j.p.min_count;
     d.ext_mode = j.p.ext_mode;
     d.t_base = j.p.t_base;
@@ -251,6 +261,11 @@ void destroy_batch(kmer_batch* b) {
         if (w.exec) cudaGraphExecDestroy(w.exec);
     for (auto& j : b->jobs)
         if (j.alone) kmer_analysis_destroy(j.alone);
+    // buffers are freed in the order of the batch's stream: before that stream goes
+    b->jobs.clear();
+    b->waves.clear();
+    DevBuf* bs[] = {&b->scratch, &b->zero, &b->misc, &b->hbm, &b->one_maps};
+    for (auto* x : bs) x->release();
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -273,6 +288,8 @@ int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_bu
         b->own_stream = true;
         CK(cudaDeviceSynchronize());  // readsets packed on the default stream are complete
     }
+    prepare_pool(b->device);
+    StreamScope scope(b->stream);
     b->jobs.resize(n_jobs);
     for (uint32_t i = 0; i < n_jobs; ++i) {
         BJob& j = b->jobs[i];
@@ -282,11 +299,7 @@ int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_bu
         TRY(plan_job(b, j));
     }
     size_t budget = memory_budget;
-    if (!budget) {
-        size_t fr = 0, tot = 0;
-        CK(cudaMemGetInfo(&fr, &tot));
-        budget = (size_t)(0.6 * (double)fr);
-    }
+    if (!budget) budget = (size_t)(0.6 * (double)free_device_bytes());
     // persistent per-job state: outputs, counters, fallback lists.  When the
     // exact upper bound (windows / min_count survivors) of every job fits in
     // 40% of the budget it is used, so no job can overflow its output.
@@ -324,7 +337,7 @@ int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_bu
         close();
     }
     TRY(b->misc.ensure(std::max<size_t>(1, n_jobs) * sizeof(Misc)));
-    TRY(b->fb.ensure(std::max<size_t>(1, n_jobs) * 64 * 4));
+    TRY(b->one_maps.ensure(4 * 8));
     TRY(b->scratch.ensure(std::max<size_t>(max_scratch, 256)));
     TRY(b->zero.ensure(std::max<size_t>(max_zero, 256)));
     b->host_misc.resize(n_jobs);
@@ -381,12 +394,99 @@ int run_alone(kmer_batch* b, BJob& j) {
 // (too many distinct keys or records for a shared-memory table): recounted
 // now, while the wave's scratch still holds their records.  Returns false if
 // the job must instead run alone (output too small for the extra survivors).
+// Grows job j's output to `cap` survivors, keeping the first `keep`, and
+// points its descriptor (host copy and the wave's device copy) at the new
+// buffers.
+int grow_output(kmer_batch* b, BJob& j, unsigned long long cap, unsigned long long keep) {
+    if (cap <= j.out_cap) return KMER_OK;
+    DevBuf nk, nc, ne, ncl;
+    TRY(nk.ensure(cap * 8 * j.W + 16));
+    TRY(nc.ensure(cap * 4 + 16));
+    TRY(ne.ensure(cap * 32 + 16));
+    TRY(ncl.ensure(cap * 2 + 16));
+    if (keep) {
+        CK(cudaMemcpyAsync(nk.p, j.out_keys.p, keep * 8 * j.W, cudaMemcpyDeviceToDevice, b->stream));
+        CK(cudaMemcpyAsync(nc.p, j.out_count.p, keep * 4, cudaMemcpyDeviceToDevice, b->stream));
+        CK(cudaMemcpyAsync(ne.p, j.out_ext.p, keep * 32, cudaMemcpyDeviceToDevice, b->stream));
+        CK(cudaMemcpyAsync(ncl.p, j.out_cls.p, keep * 2, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    j.out_keys = std::move(nk);
+    j.out_count = std::move(nc);
+    j.out_ext = std::move(ne);
+    j.out_cls = std::move(ncl);
+    j.out_cap = cap;
+    j.job.out_keys = j.out_keys.as<unsigned long long>();
+    j.job.out_count = j.out_count.as<unsigned>();
+    j.job.out_ext = j.out_ext.as<unsigned>();
+    j.job.out_cls = j.out_cls.as<unsigned char>();
+    j.job.out_cap = cap;
+    return KMER_OK;
+}
+
+int upload_desc(kmer_batch* b, BJob& j) {
+    Wave& w = b->waves[j.wave];
+    CK(cudaMemcpyAsync(w.d_jobs.as<Job>() + j.slot, &j.job, sizeof(Job), cudaMemcpyHostToDevice, b->stream));
+    return KMER_OK;
+}
+
+// Repairs job j after its wave reported an undersized output, fallback list
+// or level-2 layout: grows what was too small and re-runs, for this job
+// alone, the stages after the scatter (the level-1 records are intact).
+// *m is replaced by the job's counters after the re-run.
+int repair_job(kmer_batch* b, BJob& j, unsigned idx, Misc* m) {
+    const unsigned P = 1u << (j.g.p1 + j.g.p2);
+    const bool relayout = j.g.p2 && (m->status & (ST_L2_OVERFLOW | ST_L2_PLAN));
+    if (relayout) {
+        // every record was counted toward its leaf even when it did not fit
+        std::vector<unsigned long long> fill(P), exact(P + 1, 0);
+        CK(cudaMemcpyAsync(fill.data(), j.job.l2_fill, P * 8ull, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (unsigned i = 0; i < P; ++i) exact[i + 1] = exact[i] + fill[i];
+        if (exact[P] > j.l2_capacity) return fail(KMER_ERR_TABLE_FULL, "level-2 records exceed the job's region");
+        TRY(j.l2_exact.ensure((P + 1) * 8ull));
+        CK(cudaMemcpyAsync(j.l2_exact.p, exact.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice, b->stream));
+        j.job.l2_leaf_start = j.l2_exact.as<unsigned long long>();
+        j.job.l2_capacity = ~0ull;
+    }
+    if (m->status & ST_OUT_OVERFLOW) {
+        // without dropped records out_n is the exact survivor count
+        const unsigned long long want = relayout ? 2 * j.out_cap : m->out_n + m->out_n / 8 + 4096;
+        TRY(grow_output(b, j, std::min<unsigned long long>(want, j.windows / j.p.min_count + 1024), 0));
+    }
+    if (m->status & ST_FALLBACK_FULL) {
+        j.fb_cap = m->fb_n + 64;
+        TRY(j.fb.ensure(j.fb_cap * 4ull));
+        j.job.fb_list = j.fb.as<unsigned>();
+        j.job.fb_cap = j.fb_cap;
+    }
+    TRY(upload_desc(b, j));
+    // fresh counters, keeping the windows the scatter emitted
+    Misc z{};
+    z.stats[2] = m->stats[2];
+    CK(cudaMemcpyAsync(b->misc.as<Misc>() + idx, &z, sizeof z, cudaMemcpyHostToDevice, b->stream));
+    Wave& w = b->waves[j.wave];
+    const Job* dj = w.d_jobs.as<Job>() + j.slot;
+    unsigned long long* maps = b->one_maps.as<unsigned long long>();
+    const unsigned long long leaf_off[2] = {0ull, (unsigned long long)P};
+    CK(cudaMemcpyAsync(maps, leaf_off, 16, cudaMemcpyHostToDevice, b->stream));
+    if (relayout) {
+        CK(cudaMemsetAsync(j.job.l2_fill, 0, P * 8ull, b->stream));
+        CK(launch_l2_plan(dj, 1, maps + 2, b->stream));
+        CK(launch_repart(j.W, dj, maps + 2, 1, j.g.p2, b->num_sms, b->stream));
+    }
+    CK(launch_leaf(j.W, dj, maps, 1, P, j.cap_max, b->num_sms, b->stream));
+    CK(cudaMemcpyAsync(&b->host_misc[idx], b->misc.as<Misc>() + idx, sizeof(Misc), cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    *m = b->host_misc[idx];
+    return KMER_OK;
+}
+
 int batch_fallbacks(kmer_batch* b, BJob& j, unsigned idx, const Misc& m, bool* ok) {
     *ok = false;
     const unsigned n = m.fb_n;
     std::vector<unsigned> leaves(n);
-    CK(cudaMemcpyAsync(leaves.data(), b->fb.as<unsigned>() + 64ull * idx, n * 4ull, cudaMemcpyDeviceToHost,
-                       b->stream));
+    CK(cudaMemcpyAsync(leaves.data(), j.fb.as<unsigned>(), n * 4ull, cudaMemcpyDeviceToHost, b->stream));
     std::vector<unsigned long long> fill(n);
     const unsigned long long* fsrc = j.g.p2 ? j.job.l2_fill : j.job.l1_fill;
     CK(cudaStreamSynchronize(b->stream));
@@ -398,7 +498,10 @@ int batch_fallbacks(kmer_batch* b, BJob& j, unsigned idx, const Misc& m, bool* o
         extra += fill[i] / j.p.min_count + 1;
         max_n = std::max(max_n, fill[i]);
     }
-    if (m.out_n + extra > j.out_cap) return KMER_OK;
+    if (m.out_n + extra > j.out_cap) {  // room for the recounted leaves' survivors
+        TRY(grow_output(b, j, m.out_n + extra + (m.out_n + extra) / 8 + 4096, m.out_n));
+        TRY(upload_desc(b, j));
+    }
     const size_t eb = hbm_entry_bytes(j.W);
     TRY(b->hbm.ensure(next_pow2(std::max<unsigned long long>(1024, 2 * max_n)) * eb));
     for (unsigned i = 0; i < n; ++i) {
@@ -418,10 +521,14 @@ int batch_fallbacks(kmer_batch* b, BJob& j, unsigned idx, const Misc& m, bool* o
 
 int run_batch(kmer_batch* b) {
     const auto t0 = std::chrono::steady_clock::now();
+    StreamScope scope(b->stream);
     b->have_result = false;
     b->st.graph_launches = 0;
     b->st.jobs_alone = 0;
     b->st.fallback_leaves = 0;
+    b->st.jobs_repaired = 0;
+    b->st.alone_level1 = 0;
+    b->st.alone_other = 0;
     if (b->own_stream) CK(cudaDeviceSynchronize());  // re-packed readsets on other streams are complete
     const size_t n = b->jobs.size();
     std::vector<char> good(n, 0);
@@ -432,13 +539,25 @@ int run_batch(kmer_batch* b) {
         CK(cudaMemcpyAsync(b->host_misc.data(), b->misc.p, n * sizeof(Misc), cudaMemcpyDeviceToHost, b->stream));
         CK(cudaStreamSynchronize(b->stream));
         for (unsigned id : w.ids) {
-            const Misc& m = b->host_misc[id];
+            Misc m = b->host_misc[id];
+            BJob& j = b->jobs[id];
+            const unsigned repairable = ST_L2_OVERFLOW | ST_L2_PLAN | ST_OUT_OVERFLOW | ST_FALLBACK_FULL;
+            bool repaired = false;
+            for (int attempt = 0; attempt < 3 && m.status && !(m.status & ~repairable); ++attempt) {
+                TRY(repair_job(b, j, id, &m));
+                repaired = true;
+            }
+            if (repaired) b->st.jobs_repaired++;
             if (m.status == 0 && m.fb_n == 0 && m.stats[0] == m.stats[2]) {
                 good[id] = 1;
             } else if (m.status == 0 && m.fb_n > 0) {
                 bool ok = false;
-                TRY(batch_fallbacks(b, b->jobs[id], id, m, &ok));
+                TRY(batch_fallbacks(b, j, id, m, &ok));
                 good[id] = ok ? 1 : 0;
+            }
+            if (!good[id]) {
+                if (m.status & ST_L1_OVERFLOW) b->st.alone_level1++;
+                else b->st.alone_other++;
             }
         }
     }
@@ -454,7 +573,8 @@ int run_batch(kmer_batch* b) {
             j.n_out = m.out_n;
             j.res_windows = m.stats[0];
             j.res_distinct = m.stats[1];
-        } else {  // undersized buffer, failed wait or too large for a wave: exact regular path
+        } else {  // level-1 overflow, failed wait or too large for a wave: exact regular path
+            if (j.wave < 0) b->st.alone_other++;
             TRY(run_alone(b, j));
             b->st.jobs_alone++;
         }
@@ -545,6 +665,7 @@ int kmer_batch_destroy(kmer_batch_t* b) {
     if (!b) return KMER_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
+    StreamScope scope(b->stream);
     destroy_batch(b);
     return KMER_OK;
 }

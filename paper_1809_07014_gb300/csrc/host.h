@@ -35,16 +35,41 @@ const char* last_error_message();
         if (rc_ != KMER_OK) return rc_; \
     } while (0)
 
-// Grow-only device buffer.
+// Device allocations come from the device's stream-ordered memory pool
+// (cudaMallocAsync / cudaFreeAsync), which keeps freed memory for reuse:
+// growing or freeing a buffer neither returns memory to the driver nor
+// synchronises the device, so analyses on other streams keep running.  The
+// stream an allocation is ordered on is the calling thread's current
+// allocation stream, set by each API entry point to the stream of the object
+// it works on.
+extern thread_local cudaStream_t tl_alloc_stream;
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(tl_alloc_stream) { tl_alloc_stream = s; }
+    ~StreamScope() { tl_alloc_stream = prev; }
+    StreamScope(const StreamScope&) = delete;
+    StreamScope& operator=(const StreamScope&) = delete;
+};
+
+// Keeps the device's memory pool from trimming itself at synchronisation
+// points (once per device).
+void prepare_pool(int device);
+// Device memory available for new buffers: free memory plus what the pool
+// holds unused.
+size_t free_device_bytes();
+
+// Grow-only device buffer, allocated on and freed in the order of the stream
+// that was current when it was allocated.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t s = nullptr;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; o.bytes = 0; }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -52,18 +77,19 @@ struct DevBuf {
         if (n <= bytes && p) return KMER_OK;
         release();
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
+        s = tl_alloc_stream;
+        cudaError_t e = cudaMallocAsync(&p, n, s);
         if (e != cudaSuccess) {
             p = nullptr;
             bytes = 0;
             cudaGetLastError();
-            return fail(KMER_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+            return fail(KMER_ERR_OOM, "allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
         }
         bytes = n;
         return KMER_OK;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
         p = nullptr;
         bytes = 0;
     }
@@ -77,6 +103,11 @@ struct Misc {  // small device counters read back after each pass
     unsigned int status;
     unsigned int fb_n;
 };
+
+// Pinned host copies of Misc, from a process-wide pool (allocating and
+// freeing pinned memory would synchronise the device).
+Misc* pinned_misc_get();
+void pinned_misc_put(Misc* m);
 
 inline unsigned long long next_pow2(unsigned long long x) {
     unsigned long long p = 1;

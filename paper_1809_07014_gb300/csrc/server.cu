@@ -168,15 +168,8 @@ int kmer_server_create(uint64_t memory_budget, uint32_t workers, kmer_server_t**
         delete s;
         return fail(KMER_ERR_NO_DEVICE, "no CUDA device");
     }
-    if (!memory_budget) {
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-            cudaGetLastError();
-            delete s;
-            return fail(KMER_ERR_CUDA, "cudaMemGetInfo failed");
-        }
-        memory_budget = (uint64_t)(0.7 * (double)fr);
-    }
+    prepare_pool(s->device);
+    if (!memory_budget) memory_budget = (uint64_t)(0.7 * (double)free_device_bytes());
     s->budget = memory_budget;
     s->streams.resize(workers);
     for (unsigned i = 0; i < workers; ++i) {

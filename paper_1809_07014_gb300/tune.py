@@ -74,7 +74,7 @@ def _run(rs: ReadSet, k: int, reps: int, stream, **params) -> tuple[float, dict]
     return best, st
 
 
-def autotune(rs: ReadSet, k: int, reps: int = 2, stream=None, keys_per_leaf=(0.2, 0.3, 0.45, 0.65),
+def autotune(rs: ReadSet, k: int, reps: int = 2, stream=None, keys_per_leaf=(0.2, 0.3, 0.4, 0.5),
              l1_shifts=(-1, 0)) -> Tuning:
     """Time candidate geometries for k on readset `rs`; return the fastest."""
     ms_default, st = _run(rs, k, reps, stream)

@@ -62,9 +62,10 @@ def test_batch_matches_regular_and_oracle(samples):
     b.close()
 
 
-def test_batch_waves_and_exact_reruns(samples):
+def test_batch_waves_and_output_repairs(samples):
     """A small memory budget splits the jobs into several waves; a tiny survivor
-    hint makes outputs overflow, and those jobs are re-run exactly alone."""
+    hint makes outputs overflow, and those jobs are repaired inside their wave
+    (output grown, leaves re-run) with exact results."""
     ks = [21, 21, 33, 55, 33, 21, 55, 33]
     rsets = [pkg.ReadSet(s.bases, s.quals, s.offsets) for s in samples]
     jobs = [(r, {"k": k, "survivors_hint": 1 if i % 3 == 0 else 0}) for i, (r, k) in enumerate(zip(rsets, ks))]
@@ -82,9 +83,36 @@ def test_batch_waves_and_exact_reruns(samples):
     assert b is not None, "no budget split the jobs into waves"
     b.run()
     st = b.stats()
-    assert st["waves"] >= 2 and st["jobs_alone"] >= 1
+    assert st["waves"] >= 2 and st["jobs_repaired"] >= 1 and st["jobs_alone"] == 0
     for i, (r, k) in enumerate(zip(rsets, ks)):
         same_result(b.results(i), regular(r, k))
+    # the repaired descriptors stay: a second run needs no repair
+    b.run()
+    assert b.stats()["jobs_repaired"] == 0
+    for i, (r, k) in enumerate(zip(rsets, ks)):
+        same_result(b.results(i), regular(r, k))
+    b.close()
+
+
+def test_batch_repairs_leaf_layout_in_wave(samples):
+    """Heavy-hitter reads overflow level-2 leaves (but not the level-1 buckets):
+    the job gets an exact leaf layout and its repartition re-runs inside the
+    wave; the result equals the regular analysis and the oracle."""
+    s = samples[3]
+    heavy = np.frombuffer(bytes(s.bases[:150]), np.uint8)
+    n_heavy = 3000
+    bases = np.concatenate([s.bases, np.tile(heavy, n_heavy)])
+    quals = np.concatenate([s.quals, np.tile(s.quals[:150], n_heavy)])
+    offsets = np.concatenate([s.offsets, s.offsets[-1] + 150 * np.arange(1, n_heavy + 1, dtype=np.uint64)])
+    r = pkg.ReadSet(bases, quals, offsets)
+    b = pkg.Batch([(r, {"k": 21, "leaf_bits": 12, "l1_bits": 2})])
+    b.run()
+    st = b.stats()
+    assert st["jobs_repaired"] == 1 and st["jobs_alone"] == 0, st
+    assert_same(b.results(0), oracle.run(bases, quals, offsets, oracle.Params(k=21)), "heavy hitters")
+    b.run()  # the exact layout is kept
+    assert b.stats()["jobs_repaired"] == 0
+    assert_same(b.results(0), oracle.run(bases, quals, offsets, oracle.Params(k=21)), "heavy hitters, rerun")
     b.close()
 
 
