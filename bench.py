@@ -52,6 +52,8 @@ def parse_args():
                     help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
                          "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
     ap.add_argument("--scale", type=float, default=1.0, help="batched/serve: scale every sample size")
+    ap.add_argument("--tune", choices=["auto", "hints", "none"], default="auto",
+                    help="batched: autotuned geometry and hints, sizing hints only, or no hints")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--large", action="store_true",
                     help="serve: also run the 15-Gbase, 500-genome instance at k=55 within a 180 GB budget")
@@ -436,15 +438,22 @@ def run_batched(args):
         ka.close()
     # autotune per k on the median-size job of that k
     tunings = {}
-    for k in sorted(set(ks)):
-        idx = [i for i in range(len(ks)) if ks[i] == k]
-        mid = sorted(idx, key=lambda i: rsets[i].n_bases)[len(idx) // 2]
-        tunings[k] = autotune(rsets[mid], k, reps=1, stream=stream)
+    if args.tune != "none":
+        for k in sorted(set(ks)):
+            idx = [i for i in range(len(ks)) if ks[i] == k]
+            mid = sorted(idx, key=lambda i: rsets[i].n_bases)[len(idx) // 2]
+            tunings[k] = autotune(rsets[mid], k, reps=1, stream=stream)
     jobs = []
     for rs, k in zip(rsets, ks):
         w = rs.n_bases  # windows of 150-bp reads are ~ (150-k+1)/150 of the bases
         w = int(w * (150 - k + 1) / 150)
-        jobs.append((rs, tunings[k].params(w)))
+        if args.tune == "none":
+            jobs.append((rs, {"k": k}))
+        elif args.tune == "hints":
+            t = tunings[k].params(w)
+            jobs.append((rs, {"k": k, "distinct_hint": t["distinct_hint"], "survivors_hint": t["survivors_hint"]}))
+        else:
+            jobs.append((rs, tunings[k].params(w)))
     b = pkg.Batch(jobs, stream=stream)
     for _ in range(max(1, args.warmup)):
         b.run()
@@ -459,8 +468,8 @@ def run_batched(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"batched: {len(jobs)} synthetic metagenome samples, sizes log-uniform "
                                    f"{5 * args.scale:g}-{500 * args.scale:g} Mbases, k in {{21,33,55}}",
-                       "bases": int(sum(r.n_bases for r in rsets)), "windows": windows_all,
-                       "waves": st["waves"], "jobs_alone": st["jobs_alone"]},
+                       "bases": int(sum(r.n_bases for r in rsets)), "windows": windows_all, "tune": args.tune},
+            "batch_stats": st,
             "single_instance": {"value": windows_all / t_single, "ms_total": 1e3 * t_single,
                                 "note": "the same jobs, one regular query each, back to back"},
             "speedup_vs_single_instance": t_single / t_batch,

@@ -138,6 +138,7 @@ typedef struct {
     float ms_scatter, ms_repart, ms_leaf, ms_fallback;
     uint32_t n_scatter, n_repart, n_leaf, n_fallback;
     uint64_t records_l2;        /* records moved by the level-2 repartition */
+    uint64_t leaf_splits;       /* partitions whose keys did not fit one table and were counted in key ranges */
 } kmer_analysis_stats;
 
 /* Fills *p with defaults: min_count 2, qual_offset 33, qual_threshold 20,
@@ -203,6 +204,28 @@ int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
  * Errors: BAD_STATE (no successful query), INVALID_ARG (capacity < n). */
 int kmer_analysis_copy_results(kmer_analysis_t *h, uint64_t *keys, uint32_t *count, uint32_t *ext, uint8_t *cls,
                                uint64_t capacity);
+
+/* One looked-up k-mer (kmer_analysis_lookup), 40 bytes. */
+typedef struct {
+    uint32_t count;    /* occurrences; 0 when the k-mer is not a survivor */
+    uint32_t ext[8];   /* tallies of the canonical k-mer: left A,C,G,T then right A,C,G,T */
+    uint8_t cls[2];    /* classes of the canonical k-mer's sides (enum kmer_class) */
+    uint8_t found;     /* 1 if the k-mer is among the survivors */
+    uint8_t flipped;   /* 1 if the given k-mer is the reverse complement of its canonical form */
+} kmer_record;
+
+/* Looks up n k-mers among the survivors of the last query (the table the
+ * graph traversal of Sec. II-C consults: count and the class of each side of
+ * a vertex).  keys: n * W words, row-major, word 0 most significant, bits
+ * above 2k zero (a key with such bits is reported not found); either
+ * orientation (a k-mer and its reverse complement are one vertex, Sec.
+ * II-B).  One record per key is written to out.  keys and out are both host
+ * memory (where = KMER_HOST) or both device memory (KMER_DEVICE).  The first
+ * lookup after a query builds an index of the survivors in device memory
+ * (4 bytes per slot, 2-4 slots per survivor); later lookups reuse it.
+ * Synchronous.  Errors: BAD_STATE (no successful query), INVALID_ARG (NULL
+ * with n > 0, bad where), OOM, CUDA. */
+int kmer_analysis_lookup(kmer_analysis_t *h, const uint64_t *keys, uint64_t n, kmer_record *out, int where);
 
 /* Counters of the last query. */
 int kmer_analysis_get_stats(const kmer_analysis_t *h, kmer_analysis_stats *out);

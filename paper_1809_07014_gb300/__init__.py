@@ -69,7 +69,7 @@ class kmer_analysis_stats(ctypes.Structure):
                 ("launches", ctypes.c_uint32), ("ms_scatter", ctypes.c_float), ("ms_repart", ctypes.c_float),
                 ("ms_leaf", ctypes.c_float), ("ms_fallback", ctypes.c_float), ("n_scatter", ctypes.c_uint32),
                 ("n_repart", ctypes.c_uint32), ("n_leaf", ctypes.c_uint32), ("n_fallback", ctypes.c_uint32),
-                ("records_l2", ctypes.c_uint64)]
+                ("records_l2", ctypes.c_uint64), ("leaf_splits", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -122,6 +122,7 @@ _SIGNATURES = {
     "kmer_analysis_submit_raw": (_int, [_vp, _vp, _vp, _vp, _u64, _int]),
     "kmer_analysis_query": (_int, [_vp, ctypes.POINTER(kmer_result_view)]),
     "kmer_analysis_copy_results": (_int, [_vp, _vp, _vp, _vp, _vp, _u64]),
+    "kmer_analysis_lookup": (_int, [_vp, _vp, _u64, _vp, _int]),
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
@@ -231,6 +232,16 @@ def kmer_analysis_query(h: int) -> kmer_result_view:
     v = kmer_result_view()
     _check(load_library().kmer_analysis_query(h, ctypes.byref(v)), "kmer_analysis_query")
     return v
+
+
+# One looked-up k-mer (kmer_record, 40 bytes).
+KMER_RECORD_DTYPE = np.dtype([("count", "<u4"), ("ext", "<u4", (8,)), ("cls", "u1", (2,)), ("found", "u1"),
+                              ("flipped", "u1")])
+assert KMER_RECORD_DTYPE.itemsize == 40
+
+
+def kmer_analysis_lookup(h: int, keys: int, n: int, out: int, where: int) -> None:
+    _check(load_library().kmer_analysis_lookup(h, keys, n, out, where), "kmer_analysis_lookup")
 
 
 def kmer_analysis_copy_results(h: int, keys: int, count: int, ext: int, cls: int, capacity: int) -> None:
@@ -469,6 +480,16 @@ class KmerAnalysis:
         cls = np.empty((n, 2), dtype=np.uint8)
         kmer_analysis_copy_results(self.handle, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
         return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def lookup(self, keys) -> np.ndarray:
+        """Records (KMER_RECORD_DTYPE) of k-mers given as an (n, W) uint64 array,
+        either orientation, among the survivors of the last query."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        if keys.ndim == 1:
+            keys = keys.reshape(-1, 1)
+        out = np.zeros(len(keys), dtype=KMER_RECORD_DTYPE)
+        kmer_analysis_lookup(self.handle, _ptr(keys), len(keys), _ptr(out), KMER_HOST)
+        return out
 
     def stats(self) -> dict:
         return kmer_analysis_get_stats(self.handle).as_dict()

@@ -163,7 +163,9 @@ struct kmer_analysis {
     DevBuf l1_rec, l1_start, l1_cap, l1_fill;
     DevBuf l2_rec, l2_base, l2_leafcap, l2_fill, l2_leaf_start, tile_prefix;
     DevBuf out_keys, out_count, out_ext, out_cls;
-    DevBuf fb_list, hbm, misc;
+    DevBuf fb_list, split_list, hbm, misc;
+    DevBuf lk_index, lk_keys, lk_out;  // survivors' index for lookups, staging of host lookups
+    unsigned long long lk_cap = 0;     // index slots; 0 = no index for the current results
     DevBuf d_ajob, d_sjobs, d_tile_off, d_leaf_off, d_job_tile_off;  // job descriptors and work maps
     unsigned long long out_cap = 0, fb_cap = 0;
     Misc* host_misc = nullptr;  // pinned
@@ -186,7 +188,8 @@ struct kmer_analysis {
     size_t device_bytes() const {
         const DevBuf* bs[] = {&l1_rec, &l1_start, &l1_cap, &l1_fill, &l2_rec, &l2_base, &l2_leafcap, &l2_fill,
                               &l2_leaf_start, &tile_prefix, &out_keys, &out_count, &out_ext, &out_cls,
-                              &fb_list, &hbm, &misc, &d_ajob, &d_sjobs, &d_tile_off, &d_leaf_off,
+                              &fb_list, &split_list, &hbm, &misc, &lk_index, &lk_keys, &lk_out, &d_ajob,
+                              &d_sjobs, &d_tile_off, &d_leaf_off,
                               &d_job_tile_off};
         size_t t = 0;
         for (auto* b : bs) t += b->bytes;
@@ -402,6 +405,9 @@ void fill_job_outputs(kmer_analysis* h, Job& j) {
     j.fb_list = h->fb_list.as<unsigned int>();
     j.fb_n = &m->fb_n;
     j.fb_cap = (unsigned)h->fb_cap;
+    j.split_list = h->split_list.as<unsigned int>();
+    j.split_n = &m->split_n;
+    j.split_cap = (unsigned)(h->split_list.bytes / 4);
     j.min_count = h->p.min_count;
     j.ext_mode = h->p.ext_mode;
     j.t_base = h->p.t_base;
@@ -495,9 +501,9 @@ int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
     unsigned long long extra_out = 0, max_n = 0;
-    for (unsigned lf : leaves) {
-        extra_out += fill[lf] / h->p.min_count + 1;
-        max_n = std::max(max_n, fill[lf]);
+    for (unsigned e : leaves) {  // a range's records are at most its leaf's
+        extra_out += fill[fallback_leaf(e)] / h->p.min_count + 1;
+        max_n = std::max(max_n, fill[fallback_leaf(e)]);
     }
     TRY(read_misc(h));
     const unsigned long long out_now = h->host_misc->out_n;
@@ -507,10 +513,10 @@ int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * max_n));
     TRY(h->hbm.ensure(cap * hbm_entry_bytes(W)));
     TRY(prof_begin(h, kmer_analysis::STG_FALLBACK));
-    for (unsigned lf : leaves) {
-        const unsigned long long c = next_pow2(std::max<unsigned long long>(1024, 2 * fill[lf]));
+    for (unsigned e : leaves) {
+        const unsigned long long c = next_pow2(std::max<unsigned long long>(1024, 2 * fill[fallback_leaf(e)]));
         CK(cudaMemsetAsync(h->hbm.p, 0, c * hbm_entry_bytes(W), h->stream));
-        CK(launch_records_insert(j, lf, h->hbm.p, c, h->num_sms, h->stream));
+        CK(launch_records_insert(j, e, h->hbm.p, c, h->num_sms, h->stream));
         CK(launch_hbm_sweep(j, h->hbm.p, c, h->num_sms, h->stream));
         h->st.launches += 2;
     }
@@ -567,6 +573,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             TRY(h->fb_list.ensure(64 * 4));
             h->fb_cap = 64;
         }
+        TRY(h->split_list.ensure((size_t)P * 4));  // every leaf could need key ranges
         TRY(reset_misc(h, out_start));
         Job j{};
         j.g = g;
@@ -624,8 +631,9 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             TRY(prof_begin(h, kmer_analysis::STG_LEAF));
             CK(launch_leaf(W, h->d_ajob.as<Job>(), h->d_leaf_off.as<unsigned long long>(), 1, P, cap_max, h->num_sms,
                            h->stream));
+            CK(launch_leaf_split(W, h->d_ajob.as<Job>(), 1, cap_max, h->num_sms, h->stream));
             TRY(prof_end(h, kmer_analysis::STG_LEAF));
-            h->st.launches++;
+            h->st.launches += 2;
             TRY(read_misc(h));
             TRY(prof_collect(h));
             const Misc m = *h->host_misc;
@@ -671,6 +679,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             h->res_windows += fin.stats[0];
             h->res_distinct += fin.stats[1];
             h->st.records_emitted += fin.stats[2];
+            h->st.leaf_splits += fin.stats[3];
             if (g.p2) h->st.records_l2 += fin.stats[2];
             return KMER_OK;
         }
@@ -738,6 +747,7 @@ int run_direct(kmer_analysis* h, unsigned long long windows) {
 int do_query(kmer_analysis* h) {
     const auto t0 = std::chrono::steady_clock::now();
     h->have_result = false;
+    h->lk_cap = 0;
     h->n_out = h->res_windows = h->res_distinct = 0;
     const kmer_analysis_stats zero{};
     h->st = zero;
@@ -960,6 +970,42 @@ int kmer_analysis_copy_results(kmer_analysis_t* h, uint64_t* keys, uint32_t* cou
     return KMER_OK;
 }
 
+int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, kmer_record* out, int where) {
+    if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
+    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (n && (!keys || !out)) return fail(KMER_ERR_INVALID_ARG, "keys and out must be non-NULL when n > 0");
+    if (!h->have_result) return fail(KMER_ERR_BAD_STATE, "no successful query to look up in");
+    if (h->n_out >= 0xFFFFFFFFull) return fail(KMER_ERR_INVALID_ARG, "index limited to 2^32 - 2 survivors");
+    if (n == 0) return KMER_OK;
+    DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
+    const unsigned W = h->W();
+    if (!h->lk_cap) {  // index of the current survivors: a quarter to a half full
+        const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * h->n_out));
+        TRY(h->lk_index.ensure(cap * 4));
+        CK(cudaMemsetAsync(h->lk_index.p, 0xFF, cap * 4, h->stream));
+        CK(launch_index_build(W, h->out_keys.as<unsigned long long>(), h->n_out, h->lk_index.as<unsigned>(), cap,
+                              h->num_sms, h->stream));
+        h->lk_cap = cap;
+    }
+    const unsigned long long* dq = reinterpret_cast<const unsigned long long*>(keys);
+    kmer_record* dout = out;
+    if (where == KMER_HOST) {
+        TRY(h->lk_keys.ensure(n * 8 * W));
+        TRY(h->lk_out.ensure(n * sizeof(kmer_record)));
+        CK(cudaMemcpyAsync(h->lk_keys.p, keys, n * 8 * W, cudaMemcpyHostToDevice, h->stream));
+        dq = h->lk_keys.as<unsigned long long>();
+        dout = h->lk_out.as<kmer_record>();
+    }
+    CK(launch_lookup(W, dq, n, h->p.k, h->lk_index.as<unsigned>(), h->lk_cap, h->out_keys.as<unsigned long long>(),
+                     h->out_count.as<unsigned>(), h->out_ext.as<unsigned>(), h->out_cls.as<unsigned char>(), dout,
+                     h->num_sms, h->stream));
+    if (where == KMER_HOST)
+        CK(cudaMemcpyAsync(out, dout, n * sizeof(kmer_record), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return KMER_OK;
+}
+
 int kmer_analysis_get_stats(const kmer_analysis_t* h, kmer_analysis_stats* out) {
     if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
     *out = h->st;
@@ -975,6 +1021,7 @@ int kmer_analysis_reset(kmer_analysis_t* h) {
     h->owned.clear();
     h->have_result = false;
     h->n_out = 0;
+    h->lk_cap = 0;
     return KMER_OK;
 }
 
@@ -987,7 +1034,8 @@ int kmer_analysis_destroy(kmer_analysis_t* h) {
     kmer_analysis_reset(h);
     DevBuf* bs[] = {&h->l1_rec, &h->l1_start, &h->l1_cap, &h->l1_fill, &h->l2_rec, &h->l2_base, &h->l2_leafcap,
                     &h->l2_fill, &h->l2_leaf_start, &h->tile_prefix, &h->out_keys, &h->out_count, &h->out_ext,
-                    &h->out_cls, &h->fb_list, &h->hbm, &h->misc};
+                    &h->out_cls, &h->fb_list, &h->split_list, &h->hbm, &h->misc, &h->lk_index, &h->lk_keys,
+                    &h->lk_out};
     for (auto* b : bs) b->release();
     pinned_misc_put(h->host_misc);
     for (int i = 0; i < kmer_analysis::STG_N; ++i) {

@@ -41,8 +41,9 @@ struct BJob {
     int wave = -1;            // -1: runs alone through the regular path
     unsigned slot = 0;        // index in its wave's job array
     DevBuf out_keys, out_count, out_ext, out_cls;
-    DevBuf fb;                // fallback leaf list
+    DevBuf fb;                // fallback key ranges
     unsigned fb_cap = 64;
+    DevBuf split;             // leaves counted again in key ranges (one entry per leaf at most)
     DevBuf l2_exact;          // exact level-2 layout, once a leaf overflowed its uniform capacity
     DevBuf consts;            // level-1 bucket starts and capacities (fixed for the batch's life)
     Job job{};                // device descriptor (pointers filled per wave)
@@ -175,6 +176,10 @@ int bind_job(kmer_batch* b, BJob& j, unsigned char* scratch, unsigned char* zero
     d.fb_list = j.fb.as<unsigned>();
     d.fb_n = &m->fb_n;
     d.fb_cap = j.fb_cap;
+    TRY(j.split.ensure((size_t)P * 4));
+    d.split_list = j.split.as<unsigned>();
+    d.split_n = &m->split_n;
+    d.split_cap = P;
     d.min_count = j.p.min_count;
     d.ext_mode = j.p.ext_mode;
     d.t_base = j.p.t_base;
@@ -240,6 +245,7 @@ int capture_wave(kmer_batch* b, Wave& w) {
         const auto& c = w.classes[ci];
         e = launch_leaf(c.W, dj + c.first, maps + w.leaf_off_at[ci], c.count, c.leaves, c.cap_max, b->num_sms,
                         b->stream);
+        if (e == cudaSuccess) e = launch_leaf_split(c.W, dj + c.first, c.count, c.cap_max, b->num_sms, b->stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -475,6 +481,7 @@ int repair_job(kmer_batch* b, BJob& j, unsigned idx, Misc* m) {
         CK(launch_repart(j.W, dj, maps + 2, 1, j.g.p2, b->num_sms, b->stream));
     }
     CK(launch_leaf(j.W, dj, maps, 1, P, j.cap_max, b->num_sms, b->stream));
+    CK(launch_leaf_split(j.W, dj, 1, j.cap_max, b->num_sms, b->stream));
     CK(cudaMemcpyAsync(&b->host_misc[idx], b->misc.as<Misc>() + idx, sizeof(Misc), cudaMemcpyDeviceToHost,
                        b->stream));
     CK(cudaStreamSynchronize(b->stream));
@@ -490,8 +497,8 @@ int batch_fallbacks(kmer_batch* b, BJob& j, unsigned idx, const Misc& m, bool* o
     std::vector<unsigned long long> fill(n);
     const unsigned long long* fsrc = j.g.p2 ? j.job.l2_fill : j.job.l1_fill;
     CK(cudaStreamSynchronize(b->stream));
-    for (unsigned i = 0; i < n; ++i)
-        CK(cudaMemcpyAsync(&fill[i], fsrc + leaves[i], 8, cudaMemcpyDeviceToHost, b->stream));
+    for (unsigned i = 0; i < n; ++i)  // a range's records are at most its leaf's
+        CK(cudaMemcpyAsync(&fill[i], fsrc + fallback_leaf(leaves[i]), 8, cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     unsigned long long extra = 0, max_n = 0;
     for (unsigned i = 0; i < n; ++i) {

@@ -162,7 +162,11 @@ struct Job {
     unsigned char* out_cls;        // n * 2
     unsigned long long out_cap;
     unsigned long long* out_n;     // survivors written (atomic)
-    // overflow leaves handed to the HBM-table fallback
+    // leaves whose keys did not fit their table, counted again in key ranges
+    unsigned int* split_list;
+    unsigned int* split_n;
+    unsigned int split_cap;
+    // key ranges (fallback_entry) handed to the HBM-table fallback
     unsigned int* fb_list;
     unsigned int* fb_n;
     unsigned int fb_cap;
@@ -174,7 +178,7 @@ struct Job {
     unsigned table_ratio_num;
     // status and statistics
     unsigned int* status;
-    unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted
+    unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted, [3] leaves split
 };
 
 // ------------------------------------------------------------ classify

@@ -110,11 +110,16 @@ __global__ void __launch_bounds__(256) direct_insert_kernel(const Job j, HEntry<
     if ((threadIdx.x & 31) == 0 && windows) atomicAdd(j.stats + 0, (unsigned long long)windows);
 }
 
-// Fallback: the records of one leaf, keys rebuilt from the leaf's partition bits.
+// Fallback: the records of one key range of a leaf (fallback_entry), keys
+// rebuilt from the leaf's partition bits.  Counts the windows it inserts.
 template <int W>
-__global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const unsigned leaf, HEntry<W>* t,
+__global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const unsigned entry, HEntry<W>* t,
                                                              unsigned long long cap) {
     const Geometry g = j.g;
+    const unsigned leaf = fallback_leaf(entry), rb = fallback_rb(entry), rs = fallback_rs(entry);
+    const unsigned zb = g.zl_bits();
+    const unsigned shift = (zb > g.p2 ? zb - g.p2 : 0u) - rb;
+    const unsigned rmask = (1u << rb) - 1u;
     unsigned bucket;
     unsigned long long start, n;
     const unsigned long long* recs;
@@ -131,18 +136,23 @@ __global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const 
         n = j.l2_fill[leaf];
         recs = j.l2_rec;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(j.stats + 0, n);
+    unsigned windows = 0;
     for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
         unsigned long long key[W];
+        const unsigned long long tail = recs[(start + i) * W + W - 1];
+        if (rb && ((unsigned)((tail >> 6) >> shift) & rmask) != rs) continue;  // another range
 #pragma unroll
-        for (int w = 0; w < W; ++w) key[w] = recs[(start + i) * W + w];
-        const unsigned long long tail = key[W - 1];
+        for (int w = 0; w < W - 1; ++w) key[w] = recs[(start + i) * W + w];
         const unsigned long long z = record_z(g, j.pass, bucket, tail);
         key[W - 1] = z_to_tail<W>(z, key, g.bt);
         const unsigned e5 = (unsigned)(tail & 31ull);
         const unsigned l = e5 / 5u, r = e5 - 5u * l;
-        if (!hbm_insert<W>(t, cap, key, z, l, r, j.status)) return;
+        if (!hbm_insert<W>(t, cap, key, z, l, r, j.status)) break;
+        ++windows;
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) windows += __shfl_xor_sync(0xffffffffu, windows, o);
+    if ((threadIdx.x & 31) == 0 && windows) atomicAdd(j.stats + 0, (unsigned long long)windows);
 }
 
 // Filter, classify and compact every occupied slot (one reservation per warp).
@@ -207,14 +217,14 @@ cudaError_t launch_direct_insert(const Job& j, void* table, unsigned long long c
     return cudaGetLastError();
 }
 
-cudaError_t launch_records_insert(const Job& j, unsigned leaf, void* table, unsigned long long cap, int num_sms,
+cudaError_t launch_records_insert(const Job& j, unsigned entry, void* table, unsigned long long cap, int num_sms,
                                   cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 4;
     switch (j.g.W) {
-        case 1: records_insert_kernel<1><<<grid, 256, 0, s>>>(j, leaf, (HEntry<1>*)table, cap); break;
-        case 2: records_insert_kernel<2><<<grid, 256, 0, s>>>(j, leaf, (HEntry<2>*)table, cap); break;
-        case 3: records_insert_kernel<3><<<grid, 256, 0, s>>>(j, leaf, (HEntry<3>*)table, cap); break;
-        case 4: records_insert_kernel<4><<<grid, 256, 0, s>>>(j, leaf, (HEntry<4>*)table, cap); break;
+        case 1: records_insert_kernel<1><<<grid, 256, 0, s>>>(j, entry, (HEntry<1>*)table, cap); break;
+        case 2: records_insert_kernel<2><<<grid, 256, 0, s>>>(j, entry, (HEntry<2>*)table, cap); break;
+        case 3: records_insert_kernel<3><<<grid, 256, 0, s>>>(j, entry, (HEntry<3>*)table, cap); break;
+        case 4: records_insert_kernel<4><<<grid, 256, 0, s>>>(j, entry, (HEntry<4>*)table, cap); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

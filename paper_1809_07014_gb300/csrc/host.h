@@ -17,6 +17,12 @@
 
 namespace kmer {
 
+// Point lookups of n keys against the survivors' index (lookup.cu).
+cudaError_t launch_lookup(unsigned W, const unsigned long long* q, unsigned long long n, unsigned k,
+                          const unsigned* idx, unsigned long long cap, const unsigned long long* keys,
+                          const unsigned* count, const unsigned* ext, const unsigned char* cls, kmer_record* out,
+                          int num_sms, cudaStream_t s);
+
 // Records `code` with a formatted detail for kmer_last_error_message().
 int fail(int code, const char* fmt, ...);
 const char* last_error_message();
@@ -102,6 +108,8 @@ struct Misc {  // small device counters read back after each pass
     unsigned long long stats[4];
     unsigned int status;
     unsigned int fb_n;
+    unsigned int split_n;
+    unsigned int pad;
 };
 
 // Pinned host copies of Misc, from a process-wide pool (allocating and

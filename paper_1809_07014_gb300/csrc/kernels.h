@@ -19,8 +19,23 @@ cudaError_t launch_pack(const char* bases, const unsigned char* quals, const uns
                         const unsigned long long* blk_off, unsigned long long n, unsigned qual_offset,
                         unsigned qual_threshold, PackedBlock* out, int num_sms, cudaStream_t s);
 
+// A fallback list entry: a leaf and the key range of it to recount in HBM,
+// the records whose next `rb` z bits (below the leaf's) equal `rs`.
+constexpr unsigned kFbLeafBits = 22;
+__host__ __device__ inline unsigned fallback_entry(unsigned leaf, unsigned rb, unsigned rs) {
+    return leaf | (rb << kFbLeafBits) | (rs << (kFbLeafBits + 3));
+}
+__host__ __device__ inline unsigned fallback_leaf(unsigned e) { return e & ((1u << kFbLeafBits) - 1u); }
+__host__ __device__ inline unsigned fallback_rb(unsigned e) { return (e >> kFbLeafBits) & 7u; }
+__host__ __device__ inline unsigned fallback_rs(unsigned e) { return e >> (kFbLeafBits + 3); }
+
 // All three stages take a device array of Job descriptors (all of key width
 // W) and work over every job of the array in one launch.
+
+// Index of the survivors (positions in an open-addressing table of `cap`
+// slots, all 0xFFFFFFFF before the build) for point lookups (lookup.cu).
+cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsigned long long n, unsigned* idx,
+                               unsigned long long cap, int num_sms, cudaStream_t s);
 
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
 // tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles.
@@ -40,6 +55,10 @@ cudaError_t launch_repart(unsigned W, const Job* jobs, const unsigned long long*
 // leaf_off = exclusive prefix (n_jobs + 1) of the analyses' leaf counts.
 unsigned leaf_table_cap(unsigned W, size_t smem_budget);
 size_t leaf_smem_bytes(unsigned W, unsigned cap);
+// Leaves listed in each analysis's split list, counted in key ranges (after
+// launch_leaf, same shared-memory table).
+cudaError_t launch_leaf_split(unsigned W, const Job* jobs, unsigned n_jobs, unsigned cap_max, int num_sms,
+                              cudaStream_t s);
 cudaError_t launch_leaf(unsigned W, const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,
                         unsigned long long leaves, unsigned cap_max, int num_sms, cudaStream_t s);
 
@@ -47,7 +66,7 @@ cudaError_t launch_leaf(unsigned W, const Job* jobs, const unsigned long long* l
 // not fit on chip).  Entries are zeroed by the caller (cudaMemsetAsync 0).
 size_t hbm_entry_bytes(unsigned W);
 cudaError_t launch_direct_insert(const Job& j, void* table, unsigned long long cap, cudaStream_t s);
-cudaError_t launch_records_insert(const Job& j, unsigned leaf, void* table, unsigned long long cap, int num_sms,
+cudaError_t launch_records_insert(const Job& j, unsigned entry, void* table, unsigned long long cap, int num_sms,
                                   cudaStream_t s);
 cudaError_t launch_hbm_sweep(const Job& j, const void* table, unsigned long long cap, int num_sms, cudaStream_t s);
 

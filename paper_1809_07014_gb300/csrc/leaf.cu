@@ -31,6 +31,7 @@ constexpr unsigned kLeafFull = 1u, kLeafTimeout = 4u;
 constexpr unsigned kSpinLimit = 1u << 22;
 constexpr unsigned kMaxGroupProbes = 16;  // 64 slots; a longer chain sends the leaf to the fallback
 constexpr unsigned kLanePlanes = 5;
+constexpr unsigned kMaxSubBits = 4;       // a leaf is split into at most 16 key ranges
 
 template <int W>
 struct LeafShape {
@@ -181,6 +182,193 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
     if (r) bump(t, (unsigned)found, 4u + r);
 }
 
+// Clears slots [0, cap) of the table (all threads of the CTA).
+__device__ __forceinline__ void clear_slots(const Table& t, unsigned cap) {
+    for (unsigned s = threadIdx.x; s < cap; s += kLeafThreads) {
+        t.tail[s] = 0ull;
+#pragma unroll
+        for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * t.stride + s] = 0u;
+    }
+}
+
+// Sweeps slots [0, cap): k-mers below min_count are dropped, survivors are
+// classified and written (one output reservation per warp), and every slot
+// is left clear.  Each warp takes a slice of cap / 16 slots.
+template <int W>
+__device__ __forceinline__ void sweep_table(const Job& j, const Table& t, const LeafInfo& li, unsigned cap,
+                                            unsigned long long& distinct) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned cap_max = t.stride;
+    const unsigned per = cap / kLeafWarps;  // a multiple of 32
+    const unsigned s0 = wid * per;
+    unsigned* mylist = t.list + s0;
+    unsigned count = 0;
+    for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
+        const unsigned long long tl = t.tail[s];
+        const unsigned p0 = t.lanes[s], p1 = t.lanes[cap_max + s], p2 = t.lanes[2 * cap_max + s];
+        const unsigned c = (p0 & 0xFFFFu) + (p0 >> 16) + (p1 & 0xFFFFu) + (p1 >> 16) + (p2 & 0xFFFFu);
+        const bool ok = tl != 0ull && c >= j.min_count;
+        distinct += tl != 0ull ? 1 : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
+        } else {
+            t.tail[s] = 0ull;
+#pragma unroll
+            for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+        }
+        count += __popc(m);
+    }
+    __syncwarp();
+    unsigned long long wbase = 0;
+    if (lane == 0 && count) wbase = atomicAdd(j.out_n, (unsigned long long)count);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    for (unsigned i = lane; i < count; i += 32) {
+        const unsigned s = mylist[i];
+        const unsigned long long pos = wbase + i;
+        const unsigned long long tl = t.tail[s];
+        unsigned pl[kLanePlanes];
+#pragma unroll
+        for (unsigned p = 0; p < kLanePlanes; ++p) pl[p] = t.lanes[p * cap_max + s];
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W - 1; ++w) key[w] = t.heads[(size_t)w * cap_max + s];
+        t.tail[s] = 0ull;
+#pragma unroll
+        for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
+        if (pos >= j.out_cap) {
+            set_status(j, ST_OUT_OVERFLOW);
+            continue;
+        }
+        const unsigned nl[4] = {pl[0] & 0xFFFFu, pl[0] >> 16, pl[1] & 0xFFFFu, pl[1] >> 16};
+        const unsigned nr[4] = {pl[2] >> 16, pl[3] & 0xFFFFu, pl[3] >> 16, pl[4] & 0xFFFFu};
+        const unsigned c = nl[0] + nl[1] + nl[2] + nl[3] + (pl[2] & 0xFFFFu);
+        const unsigned long long z = record_z(j.g, j.pass, li.bucket, tl);
+        key[W - 1] = z_to_tail<W>(z, key, j.g.bt);
+#pragma unroll
+        for (int w = 0; w < W; ++w) j.out_keys[pos * W + w] = key[w];
+        j.out_count[pos] = c;
+        uint4* eo = reinterpret_cast<uint4*>(j.out_ext + pos * 8);
+        eo[0] = make_uint4(nl[0], nl[1], nl[2], nl[3]);
+        eo[1] = make_uint4(nr[0], nr[1], nr[2], nr[3]);
+        reinterpret_cast<uchar2*>(j.out_cls)[pos] = make_uchar2(classify_side(nl, c, j), classify_side(nr, c, j));
+    }
+}
+
+// A leaf whose keys did not fit its table (and that has fewer than 65 536
+// records): counted first as a whole in the whole table, then, if its keys
+// still do not fit, in key ranges.  A range (rb, rs) holds the records whose
+// next rb z bits below the leaf's bits equal rs; a range that does not fit is
+// split in two, down to kMaxSubBits levels, in depth-first order, and a range
+// that does not fit at the last level is handed to the HBM recount.  The
+// table is clean on entry and on return.  Returns the windows this thread
+// counted.
+template <int W>
+__device__ __forceinline__ unsigned count_in_ranges(const Job& j, const Table& t, const LeafInfo& li, unsigned leaf,
+                                                 unsigned* s_flags, unsigned long long* distinct) {
+    const unsigned long long n = li.n;
+    const unsigned zb = j.g.zl_bits();
+    const unsigned free_bits = zb > j.g.p2 ? zb - j.g.p2 : 0u;  // z bits below the leaf's
+    const unsigned max_rb = free_bits < kMaxSubBits ? free_bits : kMaxSubBits;
+    const unsigned cap = t.stride;
+    const unsigned long long* src = li.recs + li.start * W;
+    unsigned windows = 0;
+    unsigned rb = 0, rs = 0;
+    for (;;) {
+        const unsigned shift = free_bits - rb, rmask = (1u << rb) - 1u;
+        unsigned rwin = 0;
+        for (unsigned long long i = threadIdx.x; i < n; i += kLeafThreads) {
+            unsigned long long rec[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) rec[w] = src[i * W + w];
+            if (((unsigned)((rec[W - 1] >> 6) >> shift) & rmask) != rs) continue;
+            ++rwin;
+            if (!*(volatile unsigned*)s_flags) insert_record<W>(t, rec, cap / 4, s_flags);
+        }
+        __syncthreads();
+        const unsigned flags = *(volatile unsigned*)s_flags;
+        if (flags == kLeafFull && rb < max_rb) {  // split the range in two
+            if (threadIdx.x == 0 && rb == 0) atomicAdd(j.stats + 3, 1ull);
+            clear_slots(t, cap);
+            __syncthreads();
+            if (threadIdx.x == 0) *s_flags = 0;
+            __syncthreads();
+            ++rb;
+            rs <<= 1;
+            continue;
+        }
+        if (flags) {
+            if (threadIdx.x == 0) {
+                if (flags & kLeafTimeout) {
+                    set_status(j, ST_TIMEOUT);
+                } else {  // exact recount of the range in HBM
+                    const unsigned idx = atomicAdd(j.fb_n, 1u);
+                    if (idx < j.fb_cap) j.fb_list[idx] = fallback_entry(leaf, rb, rs);
+                    else set_status(j, ST_FALLBACK_FULL);
+                }
+            }
+            clear_slots(t, cap);
+        } else {
+            windows += rwin;
+            sweep_table<W>(j, t, li, cap, *distinct);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *s_flags = 0;
+        __syncthreads();
+        // next range in depth-first order: climb while this range was a right half
+        while (rb > 0 && (rs & 1u)) {
+            rs >>= 1;
+            --rb;
+        }
+        if (rb == 0) break;
+        ++rs;
+    }
+    return windows;
+}
+
+// Leaves whose keys did not fit their table in leaf_kernel (the split list of
+// each analysis), counted in key ranges.  Persistent CTAs over the listed
+// leaves of every analysis; each analysis's list is complete when this
+// kernel starts.
+template <int W>
+__global__ void __launch_bounds__(kLeafThreads, 2) leaf_split_kernel(const Job* __restrict__ jobs,
+                                                                    const unsigned n_jobs, const unsigned cap_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_flags;
+    const int lane = threadIdx.x & 31;
+    Table t;
+    t.stride = cap_max;
+    t.tail = reinterpret_cast<unsigned long long*>(smem);
+    t.heads = t.tail + cap_max;
+    t.lanes = reinterpret_cast<unsigned*>(t.heads + (size_t)(W - 1) * cap_max);
+    t.list = t.lanes + (size_t)kLanePlanes * cap_max;
+    bool init = false;
+    for (unsigned ji = 0; ji < n_jobs; ++ji) {
+        const Job& j = jobs[ji];
+        const unsigned n_split = *(volatile unsigned*)j.split_n;
+        if (blockIdx.x >= n_split) continue;
+        if (!init) {
+            clear_slots(t, cap_max);
+            if (threadIdx.x == 0) s_flags = 0;
+            __syncthreads();
+            init = true;
+        }
+        unsigned long long windows = 0, distinct = 0;
+        for (unsigned e = blockIdx.x; e < n_split; e += gridDim.x) {
+            const unsigned leaf = j.split_list[e];
+            const LeafInfo li = leaf_info(j, leaf);
+            windows += count_in_ranges<W>(j, t, li, leaf, &s_flags, &distinct);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            windows += __shfl_xor_sync(0xffffffffu, windows, o);
+            distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
+        }
+        if (lane == 0 && windows) atomicAdd(j.stats + 0, windows);
+        if (lane == 0 && distinct) atomicAdd(j.stats + 1, distinct);
+    }
+}
+
 // Persistent CTAs over the leaves of every analysis of key width W; `leaf_off`
 // is the exclusive prefix (n_jobs + 1) of the analyses' leaf counts.
 template <int W>
@@ -248,7 +436,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
         if (!li.ok || li.n >= 65536ull) {
             if (li.ok && threadIdx.x == 0) {  // 16-bit tallies could wrap: exact recount in HBM
                 const unsigned idx = atomicAdd(j.fb_n, 1u);
-                if (idx < j.fb_cap) j.fb_list[idx] = leaf; else set_status(j, ST_FALLBACK_FULL);
+                if (idx < j.fb_cap) j.fb_list[idx] = fallback_entry(leaf, 0, 0); else set_status(j, ST_FALLBACK_FULL);
             }
             g = ng;
             ji = nji;
@@ -288,9 +476,15 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
             if (threadIdx.x == 0) {
                 if (flags & kLeafTimeout) {
                     set_status(j, ST_TIMEOUT);
-                } else {  // keys did not fit: exact recount in HBM
-                    const unsigned idx = atomicAdd(j.fb_n, 1u);
-                    if (idx < j.fb_cap) j.fb_list[idx] = leaf; else set_status(j, ST_FALLBACK_FULL);
+                } else {  // keys did not fit: counted again, in key ranges (leaf_split_kernel)
+                    const unsigned idx = atomicAdd(j.split_n, 1u);
+                    if (idx < j.split_cap) {
+                        j.split_list[idx] = leaf;
+                    } else {
+                        const unsigned f = atomicAdd(j.fb_n, 1u);
+                        if (f < j.fb_cap) j.fb_list[f] = fallback_entry(leaf, 0, 0);
+                        else set_status(j, ST_FALLBACK_FULL);
+                    }
                 }
             }
             for (unsigned s = s0 + lane; s < s0 + per; s += 32) {  // leave the table clean
@@ -376,6 +570,29 @@ static cudaError_t launch_leaf_w(const Job* jobs, const unsigned long long* leaf
     if (grid == 0) return cudaSuccess;
     leaf_kernel<W><<<(unsigned)grid, kLeafThreads, smem, s>>>(jobs, leaf_off, n_jobs, cap_max);
     return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_leaf_split_w(const Job* jobs, unsigned n_jobs, unsigned cap_max, int num_sms,
+                                       cudaStream_t s) {
+    const size_t smem = leaf_smem_bytes(W, cap_max);
+    cudaError_t e =
+        cudaFuncSetAttribute(leaf_split_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (n_jobs == 0) return cudaSuccess;
+    leaf_split_kernel<W><<<(unsigned)num_sms * 2, kLeafThreads, smem, s>>>(jobs, n_jobs, cap_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_split(unsigned W, const Job* jobs, unsigned n_jobs, unsigned cap_max, int num_sms,
+                              cudaStream_t s) {
+    switch (W) {
+        case 1: return launch_leaf_split_w<1>(jobs, n_jobs, cap_max, num_sms, s);
+        case 2: return launch_leaf_split_w<2>(jobs, n_jobs, cap_max, num_sms, s);
+        case 3: return launch_leaf_split_w<3>(jobs, n_jobs, cap_max, num_sms, s);
+        case 4: return launch_leaf_split_w<4>(jobs, n_jobs, cap_max, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_leaf(unsigned W, const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,

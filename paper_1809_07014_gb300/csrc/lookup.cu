@@ -1,0 +1,150 @@
+// Point lookups of k-mers among the survivors of a query: the read side of
+// the k-mer table that the later stages of Algorithm 1 consult (the de
+// Bruijn graph walks of Sec. II-C ask, for a k-mer, its count and the class
+// of each side).  An index over the compacted survivors -- an open-addressing
+// table of survivor positions in HBM -- is built once per query; each lookup
+// canonicalises the given k-mer (Sec. II-B: a k-mer and its reverse
+// complement are one vertex) and probes the index.
+#include "kernels.h"
+#include "kmer_analysis.h"
+
+namespace kmer {
+
+constexpr unsigned kIdxEmpty = 0xFFFFFFFFu;
+
+template <int W>
+__device__ __forceinline__ unsigned long long key_hash(const unsigned long long (&key)[W]) {
+    unsigned long long x = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        x ^= key[w];
+        x *= 0xFF51AFD7ED558CCDull;
+        x ^= x >> 33;
+    }
+    return x;
+}
+
+// Base i (0 = first, most significant) of a k-mer held as W words, word 0
+// most significant.
+template <int W>
+__device__ __forceinline__ unsigned get_base(const unsigned long long (&key)[W], unsigned k, unsigned i) {
+    const unsigned pos = 2 * (k - 1 - i);  // bit position from the least significant end
+    return (unsigned)(key[W - 1 - pos / 64] >> (pos % 64)) & 3u;
+}
+
+template <int W>
+__device__ __forceinline__ void set_base(unsigned long long (&key)[W], unsigned k, unsigned i, unsigned b) {
+    const unsigned pos = 2 * (k - 1 - i);
+    key[W - 1 - pos / 64] |= (unsigned long long)b << (pos % 64);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) index_build_kernel(const unsigned long long* __restrict__ keys,
+                                                          unsigned long long n, unsigned* __restrict__ idx,
+                                                          unsigned long long cap) {
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = keys[i * W + w];
+        unsigned long long s = key_hash<W>(key) & (cap - 1);
+        // survivors are distinct keys: the first empty slot of the sequence is ours
+        for (unsigned long long probe = 0; probe < cap; ++probe) {
+            if (atomicCAS(idx + s, kIdxEmpty, (unsigned)i) == kIdxEmpty) break;
+            s = (s + 1) & (cap - 1);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) lookup_kernel(const unsigned long long* __restrict__ q, unsigned long long n,
+                                                     const unsigned k, const unsigned* __restrict__ idx,
+                                                     unsigned long long cap, const unsigned long long* __restrict__ keys,
+                                                     const unsigned* __restrict__ count,
+                                                     const unsigned* __restrict__ ext,
+                                                     const unsigned char* __restrict__ cls,
+                                                     kmer_record* __restrict__ out) {
+    const unsigned hb = 2 * k - 64 * (W - 1);
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
+        unsigned long long key[W], rc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            key[w] = q[i * W + w];
+            rc[w] = 0;
+        }
+        kmer_record r{};
+        const bool valid = hb >= 64 || (key[0] >> hb) == 0ull;  // no bits above 2k
+        if (valid) {
+            for (unsigned b = 0; b < k; ++b) set_base<W>(rc, k, k - 1 - b, 3u - get_base<W>(key, k, b));
+            bool flip = false;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (key[w] != rc[w]) {
+                    flip = rc[w] < key[w];
+                    break;
+                }
+            }
+            if (flip) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) key[w] = rc[w];
+            }
+            r.flipped = flip ? 1 : 0;
+            unsigned long long s = key_hash<W>(key) & (cap - 1);
+            for (unsigned long long probe = 0; probe < cap; ++probe) {
+                const unsigned p = idx[s];
+                if (p == kIdxEmpty) break;
+                bool same = true;
+#pragma unroll
+                for (int w = 0; w < W; ++w) same = same && keys[(unsigned long long)p * W + w] == key[w];
+                if (same) {
+                    r.found = 1;
+                    r.count = count[p];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) r.ext[e] = ext[(unsigned long long)p * 8 + e];
+                    r.cls[0] = cls[2ull * p];
+                    r.cls[1] = cls[2ull * p + 1];
+                    break;
+                }
+                s = (s + 1) & (cap - 1);
+            }
+        }
+        out[i] = r;
+    }
+}
+
+static unsigned grid_of(unsigned long long n, int num_sms) {
+    unsigned long long g = (n + 255) / 256, cap = (unsigned long long)num_sms * 8;
+    if (g > cap) g = cap;
+    return g ? (unsigned)g : 1u;
+}
+
+cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsigned long long n, unsigned* idx,
+                               unsigned long long cap, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned g = grid_of(n, num_sms);
+    switch (W) {
+        case 1: index_build_kernel<1><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
+        case 2: index_build_kernel<2><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
+        case 3: index_build_kernel<3><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
+        case 4: index_build_kernel<4><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lookup(unsigned W, const unsigned long long* q, unsigned long long n, unsigned k,
+                          const unsigned* idx, unsigned long long cap, const unsigned long long* keys,
+                          const unsigned* count, const unsigned* ext, const unsigned char* cls, kmer_record* out,
+                          int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned g = grid_of(n, num_sms);
+    switch (W) {
+        case 1: lookup_kernel<1><<<g, 256, 0, s>>>(q, n, k, idx, cap, keys, count, ext, cls, out); break;
+        case 2: lookup_kernel<2><<<g, 256, 0, s>>>(q, n, k, idx, cap, keys, count, ext, cls, out); break;
+        case 3: lookup_kernel<3><<<g, 256, 0, s>>>(q, n, k, idx, cap, keys, count, ext, cls, out); break;
+        case 4: lookup_kernel<4><<<g, 256, 0, s>>>(q, n, k, idx, cap, keys, count, ext, cls, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace kmer

@@ -85,6 +85,7 @@ def test_null_arguments(lib):
     assert lib.kmer_analysis_copy_results(None, None, None, None, None, 0) == pkg.KMER_ERR_INVALID_ARG
     assert lib.kmer_analysis_get_stats(None, None) == pkg.KMER_ERR_INVALID_ARG
     assert lib.kmer_analysis_reset(None) == pkg.KMER_ERR_INVALID_ARG
+    assert lib.kmer_analysis_lookup(None, None, 0, None, pkg.KMER_HOST) == pkg.KMER_ERR_INVALID_ARG
     assert lib.kmer_readset_info(None, None, None) == pkg.KMER_ERR_INVALID_ARG
     assert lib.kmer_analysis_destroy(None) == pkg.KMER_OK
     assert lib.kmer_readset_destroy(None) == pkg.KMER_OK

@@ -168,6 +168,17 @@ def test_fallback_when_leaves_do_not_fit(torch_cuda):
     assert st["fallback_leaves"] > 0
 
 
+def test_leaves_split_into_key_ranges(torch_cuda):
+    """Leaves with more distinct k-mers than a shared table holds (but fewer
+    than 65 536 records) are counted in key ranges, split by the next bits of
+    the mixed key, instead of going to the HBM recount; results stay exact."""
+    rs = synth.generate(synth.METAGENOME_2G.scaled(20_000))
+    _, st = check(rs, 31, "key ranges", leaf_bits=7)
+    assert st["leaf_splits"] > 0 and st["fallback_leaves"] == 0, st
+    _, st = check(rs, 55, "key ranges, two words", leaf_bits=7)
+    assert st["leaf_splits"] > 0, st
+
+
 def test_many_passes(torch_cuda):
     rs = synth.generate(synth.METAGENOME_2G.scaled(20_000))
     _, st = check(rs, 31, "passes", memory_budget=8 << 20)
