@@ -247,7 +247,10 @@ int kmer_analysis_destroy(kmer_analysis_t *h);
  * output or leaf layout turns out too small is repaired inside its wave (the
  * stages after the scatter re-run for that job); a job whose level-1 buckets
  * overflow, or that is too large for any wave, is re-run alone through the
- * regular path.  Results are always exact. */
+ * regular path.  Results are always exact.  A run whose counts differ much
+ * from what a job was planned for (distinct keys off by more than 25% down
+ * or 40% up) teaches the batch: the next run re-plans with those counts and
+ * re-captures the graphs. */
 typedef struct kmer_batch kmer_batch_t;
 
 typedef struct {
@@ -267,7 +270,7 @@ typedef struct {
                                  inside their wave, the later stages re-run for that job only */
     uint32_t alone_level1;    /* jobs_alone because a level-1 bucket overflowed */
     uint32_t alone_other;     /* jobs_alone for another reason (too large for a wave, a failed wait) */
-    uint32_t reserved;
+    uint32_t replans;         /* times the batch was re-planned from a run's counts (since creation) */
 } kmer_batch_stats;
 
 /* Plans the jobs, allocates every buffer (memory_budget bytes of device

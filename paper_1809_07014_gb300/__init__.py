@@ -83,7 +83,7 @@ class kmer_batch_stats(ctypes.Structure):
     _fields_ = [("jobs", ctypes.c_uint32), ("waves", ctypes.c_uint32), ("graph_launches", ctypes.c_uint32),
                 ("jobs_alone", ctypes.c_uint32), ("fallback_leaves", ctypes.c_uint32), ("ms_total", ctypes.c_float),
                 ("jobs_repaired", ctypes.c_uint32), ("alone_level1", ctypes.c_uint32), ("alone_other", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("replans", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -36,6 +36,7 @@ struct BJob {
     Geometry g{};
     unsigned W = 1, cap_max = 0;
     unsigned long long windows = 0, l1_total = 0, l2_capacity = 0, out_cap = 0;
+    unsigned long long basis = 1;  // distinct keys the geometry was planned for
     std::vector<unsigned long long> caps, starts;
     size_t scratch_bytes = 0;
     int wave = -1;            // -1: runs alone through the regular path
@@ -45,6 +46,7 @@ struct BJob {
     unsigned fb_cap = 64;
     DevBuf split;             // leaves counted again in key ranges (one entry per leaf at most)
     DevBuf l2_exact;          // exact level-2 layout, once a leaf overflowed its uniform capacity
+    unsigned exact_p1 = 0, exact_p2 = 0;  // the geometry that layout belongs to
     DevBuf consts;            // level-1 bucket starts and capacities (fixed for the batch's life)
     Job job{};                // device descriptor (pointers filled per wave)
     kmer_analysis_t* alone = nullptr;  // regular analysis used for this job, if any
@@ -84,6 +86,8 @@ struct kmer_batch {
     std::vector<Misc> host_misc;
     kmer_batch_stats st{};
     bool have_result = false;
+    size_t budget = 0;
+    bool replan = false;        // the last run's counts differ from the plan: re-plan before the next run
 };
 
 namespace {
@@ -97,6 +101,7 @@ int plan_job(kmer_batch* b, BJob& j) {
     j.cap_max = leaf_cap_for(b, j.W);
     unsigned long long basis = j.windows;
     if (p.distinct_hint) basis = std::min<unsigned long long>(p.distinct_hint, j.windows);
+    j.basis = std::max<unsigned long long>(basis, 1);
     // one pass (a batch never splits a job into passes: such jobs run alone)
     j.g = plan_geometry(p.k, std::max<unsigned long long>(j.windows, 1), std::max<unsigned long long>(basis, 1),
                         ~size_t(0) / 4, j.cap_max, p.leaf_bits, p.l1_bits);
@@ -162,6 +167,10 @@ int bind_job(kmer_batch* b, BJob& j, unsigned char* scratch, unsigned char* zero
         d.l2_fill = reinterpret_cast<unsigned long long*>(zero + z);
         z += align_up((size_t)P * 8);
         d.l2_capacity = j.l2_capacity;
+        if (j.l2_exact.p && j.exact_p1 == j.g.p1 && j.exact_p2 == j.g.p2) {  // a layout learned by a repair
+            d.l2_leaf_start = j.l2_exact.as<unsigned long long>();
+            d.l2_capacity = ~0ull;
+        }
     }
     d.out_keys = j.out_keys.as<unsigned long long>();
     d.out_count = j.out_count.as<unsigned>();
@@ -276,36 +285,21 @@ void destroy_batch(kmer_batch* b) {
     delete b;
 }
 
-int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_budget, cudaStream_t stream,
-                 kmer_batch** out) {
-    auto* b = new (std::nothrow) kmer_batch;
-    if (!b) return fail(KMER_ERR_OOM, "host allocation failed");
-    std::unique_ptr<kmer_batch, void (*)(kmer_batch*)> guard(b, destroy_batch);
-    CK(cudaGetDevice(&b->device));
-    int smem_sm = 0, smem_optin = 0;
-    CK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device));
-    CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device));
-    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-    b->leaf_budget = std::min<size_t>((size_t)smem_optin, (size_t)smem_sm / 2 - 1024 - 256);
-    if (stream) {
-        b->stream = stream;
-    } else {
-        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
-        b->own_stream = true;
-        CK(cudaDeviceSynchronize());  // readsets packed on the default stream are complete
-    }
-    prepare_pool(b->device);
-    StreamScope scope(b->stream);
-    b->jobs.resize(n_jobs);
-    for (uint32_t i = 0; i < n_jobs; ++i) {
-        BJob& j = b->jobs[i];
-        j.rs = jobs[i].readset;
-        j.p = jobs[i].params;
-        j.survivors_hint = jobs[i].survivors_hint;
+// Plans every job (geometry and buffer sizes from its parameters and
+// hints), groups the jobs into waves that fit the budget, binds their
+// descriptors and captures one graph per wave.  Called at creation and again
+// when a run's counts show that the plan was off.
+int build_plan(kmer_batch* b) {
+    const unsigned n_jobs = (unsigned)b->jobs.size();
+    for (auto& w : b->waves)
+        if (w.exec) cudaGraphExecDestroy(w.exec);
+    b->waves.clear();
+    for (auto& j : b->jobs) {
+        j.wave = -1;
+        j.slot = 0;
         TRY(plan_job(b, j));
     }
-    size_t budget = memory_budget;
-    if (!budget) budget = (size_t)(0.6 * (double)free_device_bytes());
+    const size_t budget = b->budget;
     // persistent per-job state: outputs, counters, fallback lists.  When the
     // exact upper bound (windows / min_count survivors) of every job fits in
     // 40% of the budget it is used, so no job can overflow its output.
@@ -375,6 +369,38 @@ int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_bu
     }
     b->st.jobs = n_jobs;
     b->st.waves = (uint32_t)b->waves.size();
+    return KMER_OK;
+}
+
+int create_batch(const kmer_batch_job* jobs, uint32_t n_jobs, uint64_t memory_budget, cudaStream_t stream,
+                 kmer_batch** out) {
+    auto* b = new (std::nothrow) kmer_batch;
+    if (!b) return fail(KMER_ERR_OOM, "host allocation failed");
+    std::unique_ptr<kmer_batch, void (*)(kmer_batch*)> guard(b, destroy_batch);
+    CK(cudaGetDevice(&b->device));
+    int smem_sm = 0, smem_optin = 0;
+    CK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device));
+    CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device));
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    b->leaf_budget = std::min<size_t>((size_t)smem_optin, (size_t)smem_sm / 2 - 1024 - 256);
+    if (stream) {
+        b->stream = stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+        CK(cudaDeviceSynchronize());  // readsets packed on the default stream are complete
+    }
+    prepare_pool(b->device);
+    StreamScope scope(b->stream);
+    b->jobs.resize(n_jobs);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        BJob& j = b->jobs[i];
+        j.rs = jobs[i].readset;
+        j.p = jobs[i].params;
+        j.survivors_hint = jobs[i].survivors_hint;
+    }
+    b->budget = memory_budget ? memory_budget : (size_t)(0.6 * (double)free_device_bytes());
+    TRY(build_plan(b));
     guard.release();
     *out = b;
     return KMER_OK;
@@ -453,6 +479,8 @@ int repair_job(kmer_batch* b, BJob& j, unsigned idx, Misc* m) {
         CK(cudaMemcpyAsync(j.l2_exact.p, exact.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice, b->stream));
         j.job.l2_leaf_start = j.l2_exact.as<unsigned long long>();
         j.job.l2_capacity = ~0ull;
+        j.exact_p1 = j.g.p1;
+        j.exact_p2 = j.g.p2;
     }
     if (m->status & ST_OUT_OVERFLOW) {
         // without dropped records out_n is the exact survivor count
@@ -536,6 +564,11 @@ int run_batch(kmer_batch* b) {
     b->st.jobs_repaired = 0;
     b->st.alone_level1 = 0;
     b->st.alone_other = 0;
+    if (b->replan) {  // sizing learned from the previous run
+        TRY(build_plan(b));
+        b->replan = false;
+        b->st.replans++;
+    }
     if (b->own_stream) CK(cudaDeviceSynchronize());  // re-packed readsets on other streams are complete
     const size_t n = b->jobs.size();
     std::vector<char> good(n, 0);
@@ -584,6 +617,26 @@ int run_batch(kmer_batch* b) {
             if (j.wave < 0) b->st.alone_other++;
             TRY(run_alone(b, j));
             b->st.jobs_alone++;
+        }
+    }
+    // sizing for the next run: a job whose distinct keys were far from what its
+    // geometry was planned for gets its counts as hints (its leaves keep the
+    // planned number of keys each), and the batch is re-planned before that run
+    for (size_t i = 0; i < n; ++i) {
+        BJob& j = b->jobs[i];
+        // a job with a learned exact leaf layout keeps its plan
+        if (j.windows == 0 || j.used_alone || !good[i] || j.l2_exact.p) continue;
+        const double r = (double)j.res_distinct / (double)j.basis;
+        if (r > 1.25 || r < 0.6) {
+            if (j.p.leaf_bits) {
+                const double per_leaf = (double)j.basis / (double)(1ull << j.p.leaf_bits);
+                unsigned lb = ceil_log2((unsigned long long)std::max(2.0, (double)j.res_distinct / per_leaf));
+                j.p.leaf_bits = std::min(22u, std::max(1u, lb));
+                j.p.l1_bits = 0;
+            }
+            j.p.distinct_hint = j.res_distinct + j.res_distinct / 16 + 1;
+            j.survivors_hint = j.n_out;
+            b->replan = true;
         }
     }
     b->st.ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();

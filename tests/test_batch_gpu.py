@@ -86,9 +86,15 @@ def test_batch_waves_and_output_repairs(samples):
     assert st["waves"] >= 2 and st["jobs_repaired"] >= 1 and st["jobs_alone"] == 0
     for i, (r, k) in enumerate(zip(rsets, ks)):
         same_result(b.results(i), regular(r, k))
-    # the repaired descriptors stay: a second run needs no repair
+    # the second run may re-plan from the first run's counts (and repair under
+    # the new plan); after that the plan and the repaired descriptors hold
     b.run()
-    assert b.stats()["jobs_repaired"] == 0
+    for i, (r, k) in enumerate(zip(rsets, ks)):
+        same_result(b.results(i), regular(r, k))
+    replans = b.stats()["replans"]
+    b.run()
+    st = b.stats()
+    assert st["jobs_repaired"] == 0 and st["jobs_alone"] == 0 and st["replans"] == replans
     for i, (r, k) in enumerate(zip(rsets, ks)):
         same_result(b.results(i), regular(r, k))
     b.close()
@@ -110,8 +116,8 @@ def test_batch_repairs_leaf_layout_in_wave(samples):
     st = b.stats()
     assert st["jobs_repaired"] == 1 and st["jobs_alone"] == 0, st
     assert_same(b.results(0), oracle.run(bases, quals, offsets, oracle.Params(k=21)), "heavy hitters")
-    b.run()  # the exact layout is kept
-    assert b.stats()["jobs_repaired"] == 0
+    b.run()  # the exact layout is kept (and the job keeps its plan)
+    assert b.stats()["jobs_repaired"] == 0 and b.stats()["replans"] == 0
     assert_same(b.results(0), oracle.run(bases, quals, offsets, oracle.Params(k=21)), "heavy hitters, rerun")
     b.close()
 
@@ -127,4 +133,24 @@ def test_batch_of_empty_and_tiny_jobs():
     b.run()
     assert len(b.results(0)) == 0 and len(b.results(2)) == 0
     assert_same(b.results(1), oracle.run(bases, quals, offsets, oracle.Params(k=5, min_count=1)), "tiny")
+    b.close()
+
+
+def test_batch_replans_from_its_counts(samples):
+    """Hints far from the truth (100 distinct k-mers) give a coarse plan whose
+    leaves overflow and are counted in key ranges; the run's counts re-plan
+    the batch, and every run is exact."""
+    ks = [21, 33, 55, 21]
+    rsets = [pkg.ReadSet(s.bases, s.quals, s.offsets) for s in samples[:4]]
+    b = pkg.Batch([(r, {"k": k, "distinct_hint": 100}) for r, k in zip(rsets, ks)])
+    b.run()
+    assert b.stats()["replans"] == 0
+    first = [b.results(i) for i in range(4)]
+    b.run()
+    assert b.stats()["replans"] == 1
+    for i, (r, k) in enumerate(zip(rsets, ks)):
+        same_result(b.results(i), regular(r, k))
+        same_result(first[i], regular(r, k))
+    b.run()
+    assert b.stats()["replans"] == 1  # the learned plan holds
     b.close()
