@@ -217,6 +217,16 @@ int validate_params(const kmer_analysis_params* p) {
     return KMER_OK;
 }
 
+// Device address of page-locked host memory, or null for any other pointer.
+const void* host_mapped(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
                  uint64_t n_reads, int where, cudaStream_t s) {
     rs->n_reads = 0;
@@ -229,20 +239,24 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
     const uint8_t* d_quals = quals;
     TRY(rs->offsets.ensure((n_reads + 1) * 8));
     if (where == KMER_HOST) {
-        for (uint64_t i = 0; i < n_reads; ++i) {
-            if (offsets[i + 1] < offsets[i])
-                return fail(KMER_ERR_INVALID_ARG, "offsets decrease at read %llu", (unsigned long long)i);
-            if (offsets[i + 1] - offsets[i] >= 0x80000000ull)
-                return fail(KMER_ERR_INVALID_ARG, "read %llu is 2^31 bases or longer", (unsigned long long)i);
-        }
-        const unsigned long long nb = offsets[n_reads];
-        TRY(rs->tmp_bases.ensure(nb + 16));
-        TRY(rs->tmp_quals.ensure(nb + 16));
-        CK(cudaMemcpyAsync(rs->tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(rs->tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
+        // offsets are checked on the device (read_geometry_kernel)
         CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
-        d_bases = rs->tmp_bases.as<char>();
-        d_quals = rs->tmp_quals.as<uint8_t>();
+        // page-locked host memory is read in place by the pack kernel over the
+        // host link (one pass, no staging copy); other host memory is staged
+        const char* mb = static_cast<const char*>(host_mapped(bases));
+        const uint8_t* mq = static_cast<const uint8_t*>(host_mapped(quals));
+        if (mb && mq) {
+            d_bases = mb;
+            d_quals = mq;
+        } else {
+            const unsigned long long nb = offsets[n_reads];
+            TRY(rs->tmp_bases.ensure(nb + 16));
+            TRY(rs->tmp_quals.ensure(nb + 16));
+            CK(cudaMemcpyAsync(rs->tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(rs->tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
+            d_bases = rs->tmp_bases.as<char>();
+            d_quals = rs->tmp_quals.as<uint8_t>();
+        }
     } else {
         CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyDeviceToDevice, s));
     }
