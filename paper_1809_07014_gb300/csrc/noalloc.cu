@@ -60,7 +60,9 @@ __host__ __device__ inline unsigned long long na_max_bases(unsigned W) { return 
 template <int W>
 __device__ bool na_insert(NaEntry<W>* t, unsigned long long cap, const unsigned long long (&key)[W],
                           unsigned long long z, unsigned lcode, unsigned rcode, NaCounters* c) {
-    unsigned long long slot = z & (cap - 1);
+    // home slot from the top bits of a multiplicative hash of z (the low bits
+    // of a one-word z depend only on the low bits of the key)
+    unsigned long long slot = (z * 0x9E3779B97F4A7C15ull) >> (__clzll(cap) + 1);
     const unsigned long long k0 = key[0] | kNaOcc;
     for (unsigned long long probe = 0; probe < cap; ++probe) {
         NaEntry<W>* e = t + slot;

@@ -54,7 +54,7 @@ __device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long l
     const unsigned pass = j.pass;
     unsigned emitted = 0;
     for (unsigned long long round = 0; round < rounds; ++round) {
-#pragma unroll 1
+#pragma unroll 2
         for (unsigned s = 0; s < R; ++s) {
             const unsigned long long t = round * R + s;
             const unsigned e = s * kStageThreads + threadIdx.x;
