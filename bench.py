@@ -72,19 +72,35 @@ def load_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def kernel_traffic(name: str, src: str):
+# Source files each kernel is compiled from (its .cu and the headers it includes).
+KERNEL_SOURCES = {
+    "pack_kernel": ["pack.cu", "common.cuh", "kernels.h"],
+    "scatter_kernel": ["scatter.cu", "stage.cuh", "roll.cuh", "common.cuh", "kernels.h"],
+    "repart_kernel": ["repart.cu", "stage.cuh", "common.cuh", "kernels.h"],
+    "leaf_kernel": ["leaf.cu", "roll.cuh", "common.cuh", "kernels.h"],
+    "direct_insert_kernel": ["hbm.cu", "roll.cuh", "common.cuh", "kernels.h"],
+}
+
+
+def kernel_source_sha(name: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[name]:
+        h.update(open(os.path.join(ROOT, "paper_1809_07014_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(name: str, src: str = ""):
     """Per-launch DRAM bytes of a kernel from its committed ncu summary, or None
-    when the summary is missing or the kernel source changed since."""
+    when the summary is missing or the kernel's sources changed since."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or name not in KERNEL_SOURCES:
         return None
     text = open(path).read()
     m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_bytes = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.e+]+)", text)
     if not m_sha or not m_bytes:
         return None
-    cur = hashlib.sha256(open(os.path.join(ROOT, "paper_1809_07014_gb300", "csrc", src), "rb").read()).hexdigest()
-    return float(m_bytes.group(1)) if cur == m_sha.group(1) else None
+    return float(m_bytes.group(1)) if kernel_source_sha(name) == m_sha.group(1) else None
 
 
 class Clocks:
