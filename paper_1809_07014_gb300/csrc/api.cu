@@ -182,6 +182,7 @@ struct kmer_analysis {
     unsigned hist_k = 0;
     double hist_ratio = 0.0;
     unsigned l2_slack_num = 512;  // leaf capacity = 2 * mean + 256
+    double hint_ratio = 0.0;      // distinct_hint / windows of the current query (0 = no hint)
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -364,10 +365,7 @@ Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget
     if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
     else if (h->hist_k == h->p.k && h->hist_ratio > 0.0)  // learned from the previous query at this k
         basis = std::min<unsigned long long>(windows, (unsigned long long)(1.15 * h->hist_ratio * (double)windows) + 1);
-    unsigned l1 = h->p.l1_bits;
-    if (!l1)
-        if (const char* e = getenv("KMER_L1_BITS")) l1 = (unsigned)atoi(e);  // tuning experiments only
-    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, l1);
+    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, h->p.l1_bits);
     pl.passes = 1u << pl.g.ps;
     return pl;
 }
@@ -432,6 +430,7 @@ void fill_job_outputs(kmer_analysis* h, Job& j) {
     // leaf table: twice the expected distinct keys of a leaf (one slot per record if unknown)
     double ratio = 1.0;
     if (h->hist_k == h->p.k && h->hist_ratio > 0.0) ratio = std::min(1.0, 2.0 * h->hist_ratio + 0.05);
+    else if (h->hint_ratio > 0.0) ratio = std::min(1.0, 2.0 * h->hint_ratio + 0.05);
     j.table_ratio_num = (unsigned)(ratio * 65536.0);
 }
 
@@ -786,6 +785,7 @@ int do_query(kmer_analysis* h) {
             TRY(ensure_output(h, std::min(bound, want), 0));
             // the records of a pass get what the output leaves of the budget
             const size_t out_bytes = (size_t)(h->out_cap * out_bytes_per);
+            h->hint_ratio = h->p.distinct_hint ? std::min(1.0, (double)h->p.distinct_hint / (double)windows) : 0.0;
             const Plan pl = make_plan(h, windows, budget > 2 * out_bytes ? budget - out_bytes : budget / 2, cap_max);
             h->st.pass_bits = pl.g.ps;
             h->st.l1_bits = pl.g.p1;
@@ -821,6 +821,11 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+void kmer::analysis_set_sizing(kmer_analysis_t* h, uint64_t memory_budget, uint64_t distinct_hint) {
+    h->p.memory_budget = memory_budget;
+    h->p.distinct_hint = distinct_hint;
+}
 
 // ====================================================================== C ABI
 extern "C" {

@@ -128,6 +128,10 @@ inline unsigned ceil_log2(unsigned long long x) {
     return b;
 }
 
+// Resizing hints of an existing analysis (its memory budget and expected
+// distinct k-mers), for a pooled analysis taken by another request.
+void analysis_set_sizing(kmer_analysis_t* h, uint64_t memory_budget, uint64_t distinct_hint);
+
 // Partition geometry for one analysis: k-mer words, pass bits and level bits.
 // basis = expected distinct keys (or windows), cap_max = leaf table slots,
 // leaf_bits / l1_bits = overrides (0 = automatic).

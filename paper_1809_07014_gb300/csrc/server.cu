@@ -47,8 +47,14 @@ struct Pooled {
     unsigned worker;  // an analysis stays on the stream of the worker that created it
 };
 
-bool same_params(const kmer_analysis_params& a, const kmer_analysis_params& b) {
-    return std::memcmp(&a, &b, sizeof a) == 0;
+// Parameters that decide a result (and the partition geometry overrides):
+// a pooled analysis with the same ones serves the request after its sizing
+// hints (memory budget, distinct keys) are set to the request's.
+bool compatible(const kmer_analysis_params& a, const kmer_analysis_params& b) {
+    return a.k == b.k && a.min_count == b.min_count && a.qual_offset == b.qual_offset &&
+           a.qual_threshold == b.qual_threshold && a.ext_mode == b.ext_mode && a.t_base == b.t_base &&
+           a.err_num == b.err_num && a.err_den == b.err_den && a.t_ext == b.t_ext && a.variant == b.variant &&
+           a.leaf_bits == b.leaf_bits && a.l1_bits == b.l1_bits && a.flags == b.flags;
 }
 
 }  // namespace
@@ -65,6 +71,7 @@ struct kmer_server {
     std::vector<Pooled> pool;       // released analyses kept for reuse
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    double ratio[KMER_MAX_K + 1] = {};  // distinct / windows of the last finished request at each k
     uint64_t next_id = 1;
     bool stop = false;
     unsigned running = 0;
@@ -119,7 +126,7 @@ void worker(kmer_server* s, unsigned wi) {
         // an idle analysis with the same parameters carries its buffers over
         kmer_analysis_t* h = nullptr;
         for (size_t i = 0; i < s->pool.size(); ++i) {
-            if (s->pool[i].worker == wi && same_params(s->pool[i].p, r->p)) {
+            if (s->pool[i].worker == wi && compatible(s->pool[i].p, r->p)) {
                 h = s->pool[i].h;
                 s->in_use -= s->pool[i].bytes;  // the request's footprint now covers it
                 s->pool.erase(s->pool.begin() + (long)i);
@@ -134,12 +141,15 @@ void worker(kmer_server* s, unsigned wi) {
         if (!h) {
             rc = kmer_analysis_create(&r->p, stream, &h);
         } else {
+            analysis_set_sizing(h, r->p.memory_budget, r->p.distinct_hint);
             rc = kmer_analysis_reset(h);
         }
         if (rc == KMER_OK) rc = kmer_analysis_submit(h, r->rs);
         if (rc == KMER_OK) rc = kmer_analysis_query(h, &r->view);
         std::string err = rc == KMER_OK ? std::string() : std::string(kmer_last_error_message());
         lk.lock();
+        if (rc == KMER_OK && r->view.windows)
+            s->ratio[r->p.k] = (double)r->view.distinct / (double)r->view.windows;
         s->running--;
         r->h = h;
         r->worker = wi;
@@ -200,6 +210,9 @@ int kmer_server_submit(kmer_server_t* s, const kmer_readset_t* rs, const kmer_an
         std::lock_guard<std::mutex> lk(s->mu);
         r->footprint = estimate_footprint(rs, *p, s->budget);
         if (!r->p.memory_budget || r->p.memory_budget > r->footprint) r->p.memory_budget = r->footprint;
+        // distinct keys expected from the last request at this k (sizes the partitions)
+        if (!r->p.distinct_hint && s->ratio[p->k] > 0.0)
+            r->p.distinct_hint = (uint64_t)(1.1 * s->ratio[p->k] * (double)rs->windows_for(p->k)) + 1;
         r->id = s->next_id++;
         r->t_submit = s->now_ms();
         *id = r->id;

@@ -87,3 +87,21 @@ def test_bad_request_rejected(readsets):
         srv.submit(readsets[0], 22)
     assert e.value.code == pkg.KMER_ERR_INVALID_ARG
     srv.close()
+
+
+def test_pooled_analysis_serves_other_readsets_at_the_same_k(readsets):
+    """A released analysis is reused by a later request with the same result
+    parameters (same k) on another readset of another size; the server's
+    learned distinct ratio sizes it, and the result is exact."""
+    srv = pkg.Server(workers=1)
+    rid = srv.submit(readsets[0], 21)
+    srv.wait(rid)
+    srv.release(rid)
+    assert srv.stats()["pooled"] == 1
+    for i in (3, 2):
+        rid = srv.submit(readsets[i], 21)
+        srv.wait(rid)
+        assert srv.stats()["pooled"] == 0  # the pooled analysis was taken
+        same_result(srv.results(rid), alone(readsets[i], 21))
+        srv.release(rid)
+    srv.close()
