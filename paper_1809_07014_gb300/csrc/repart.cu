@@ -7,6 +7,8 @@
 
 namespace kmer {
 
+constexpr unsigned kRepartThreads = 512;
+
 template <int W>
 struct RepartShape {
     static constexpr unsigned S = W == 1 ? 4096 : (W == 2 ? 2048 : 1024);  // records per tile
@@ -139,14 +141,14 @@ __device__ __forceinline__ RepartTile repart_tile_at(const Job* __restrict__ job
 // loads overlap the flush.  Shared memory is laid out for `pmax` leaves per
 // bucket, the largest fan-out of the launch.
 template <int W, unsigned MAXPER>
-__global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __restrict__ jobs,
                                                                  const unsigned long long* __restrict__ job_tile_off,
                                                                  const unsigned n_jobs, const unsigned pmax) {
     constexpr unsigned S = RepartShape<W>::S;
-    constexpr unsigned U = S / kStageThreads;
+    constexpr unsigned U = S / kRepartThreads;
     extern __shared__ __align__(16) unsigned char smem[];
     const StageBufs b = carve_stage(smem, W, S, pmax);
-    for (unsigned d = threadIdx.x; d < pmax; d += kStageThreads) b.hist[d] = 0;
+    for (unsigned d = threadIdx.x; d < pmax; d += kRepartThreads) b.hist[d] = 0;
     const unsigned long long all = job_tile_off[n_jobs];
     unsigned long long gt = blockIdx.x;
     unsigned long long rec[U][W];
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __r
     auto load = [&](const RepartTile& x) {
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
-            const unsigned e = u * kStageThreads + threadIdx.x;
+            const unsigned e = u * kRepartThreads + threadIdx.x;
 #pragma unroll
             for (int w = 0; w < W; ++w) rec[u][w] = e < x.cnt ? __ldcs(x.src + (size_t)e * W + w) : 0ull;
         }
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __r
         const unsigned shift = zb - j.g.p2;
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
-            const unsigned e = u * kStageThreads + threadIdx.x;
+            const unsigned e = u * kRepartThreads + threadIdx.x;
             unsigned m = 0xFFFFFFFFu;
             if (e < rt.cnt) {
                 const unsigned long long zl = rec[u][W - 1] >> 6;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) repart_kernel(const Job* __r
             load(nrt);
         }
         L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[rt.bucket], j.l2_leafcap[rt.bucket], rt.bucket << j.g.p2};
-        flush_stage<W, MAXPER>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
+        flush_stage<W, MAXPER, L2Dest, kRepartThreads>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
         gt = ngt;
         rt = nrt;
     }
@@ -215,16 +217,16 @@ static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* j
     cudaError_t e =
         cudaFuncSetAttribute(repart_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    repart_kernel<W, MAXPER><<<num_sms * 2, kStageThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
+    repart_kernel<W, MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
     return cudaGetLastError();
 }
 
 template <int W>
 static cudaError_t launch_repart_w(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
                                    unsigned max_p2, int num_sms, cudaStream_t s) {
-    if ((1u << max_p2) <= 2 * kStageThreads)
+    if ((1u << max_p2) <= 2 * kRepartThreads)
         return launch_repart_wp<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
-    return launch_repart_wp<W, kMaxStageDest / kStageThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+    return launch_repart_wp<W, kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
 }
 
 cudaError_t launch_repart(unsigned W, const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,

@@ -12,8 +12,11 @@ namespace kmer {
 constexpr int kStageThreads = 256;
 constexpr unsigned kMaxStageDest = 2048;  // destinations of one staging round (partition fan-out)
 
-// Exclusive scan across the 256 threads of the block (all must call).
+// Exclusive scan across the NT threads of the block (all must call;
+// warp_tmp holds NT / 32 words).
+template <unsigned NT = kStageThreads>
 __device__ inline unsigned block_scan_u32(unsigned v, unsigned* warp_tmp, unsigned* total) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned x = v;
 #pragma unroll
@@ -24,17 +27,17 @@ __device__ inline unsigned block_scan_u32(unsigned v, unsigned* warp_tmp, unsign
     if (lane == 31) warp_tmp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        unsigned s = lane < kStageThreads / 32 ? warp_tmp[lane] : 0u;
+        unsigned s = lane < (int)(NT / 32) ? warp_tmp[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < kStageThreads / 32) warp_tmp[lane] = s;
+        if (lane < (int)(NT / 32)) warp_tmp[lane] = s;
     }
     __syncthreads();
     const unsigned before = wid ? warp_tmp[wid - 1] : 0u;
-    *total = warp_tmp[kStageThreads / 32 - 1];
+    *total = warp_tmp[NT / 32 - 1];
     __syncthreads();
     return before + x - v;
 }
@@ -75,11 +78,11 @@ struct StageBufs {
     unsigned* hist;              // P
     unsigned* lbase;             // P
     unsigned* order;             // S: (destination << 16) | staged index, per sorted position
-    unsigned* warp_tmp;          // 8
+    unsigned* warp_tmp;          // one word per warp of the block (up to 32)
 };
 
 __host__ __device__ inline size_t stage_smem_bytes(unsigned W, unsigned S, unsigned P) {
-    return (size_t)S * W * 8 + (size_t)P * 8 + (size_t)P * 4 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 4 + 64;
+    return (size_t)S * W * 8 + (size_t)P * 8 + (size_t)P * 4 + (size_t)S * 4 + (size_t)P * 8 + (size_t)S * 4 + 128;
 }
 
 __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigned S, unsigned P) {
@@ -106,45 +109,59 @@ __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigne
 // says which staged record goes there and to which destination, and
 // consecutive threads write consecutive positions, i.e. contiguous runs per
 // destination.
-template <int W, unsigned MAXPER, class Dest>
+template <int W, unsigned MAXPER, class Dest, unsigned NT = kStageThreads>
 __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
                             unsigned* status, unsigned overflow_bit) {
     __syncthreads();
     // exclusive scan of hist -> lbase (each thread owns a run of consecutive destinations)
-    const unsigned per = (P + kStageThreads - 1) / kStageThreads;
+    const unsigned per = (P + NT - 1) / NT;
     const unsigned d0 = threadIdx.x * per;
     unsigned mine = 0;
     for (unsigned i = 0; i < per; ++i)
         if (d0 + i < P) mine += b.hist[d0 + i];
     unsigned total;
-    unsigned run = block_scan_u32(mine, b.warp_tmp, &total);
-    // reservations of this thread's destinations are independent: unrolled so
-    // that all of them are in flight together
-    bool over = false;
+    const unsigned run0 = block_scan_u32<NT>(mine, b.warp_tmp, &total);
+    // reservations of this thread's destinations are independent: all are
+    // issued together, and their results are only used after the sort below
+    // (which needs just the local bases), so the atomics' latency overlaps it
+    unsigned long long first[MAXPER];
+    unsigned hs[MAXPER];
+    unsigned run = run0;
 #pragma unroll
     for (unsigned i = 0; i < MAXPER; ++i) {
         const unsigned d = d0 + i;
+        hs[i] = 0;
+        first[i] = 0;
         if (i < per && d < P) {
-            const unsigned h = b.hist[d];
+            hs[i] = b.hist[d];
             b.lbase[d] = run;
-            if (h) {
-                const unsigned long long first = dest.reserve(d, h), cap = dest.cap(d);
-                b.wbase[d] = dest.start(d) + first - run;
-                // positions of d that still fit: [run, run + min(h, cap - first))
-                const unsigned long long room = first < cap ? cap - first : 0ull;
-                b.ok_end[d] = run + (unsigned)(room < h ? room : h);
-                over = over || room < h;
-            }
-            run += h;
+            if (hs[i]) first[i] = dest.reserve(d, hs[i]);
+            run += hs[i];
         }
     }
     __syncthreads();
-    for (unsigned e = threadIdx.x; e < S; e += kStageThreads) {
+    for (unsigned e = threadIdx.x; e < S; e += NT) {
         const unsigned m = b.meta[e];
         if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (m & 0xFFFF0000u) | e;
     }
+    bool over = false;
+    run = run0;
+#pragma unroll
+    for (unsigned i = 0; i < MAXPER; ++i) {
+        const unsigned d = d0 + i;
+        const unsigned h = hs[i];
+        if (h) {
+            const unsigned long long cap = dest.cap(d);
+            b.wbase[d] = dest.start(d) + first[i] - run;
+            // positions of d that still fit: [run, run + min(h, cap - first))
+            const unsigned long long room = first[i] < cap ? cap - first[i] : 0ull;
+            b.ok_end[d] = run + (unsigned)(room < h ? room : h);
+            over = over || room < h;
+        }
+        run += h;
+    }
     __syncthreads();
-    for (unsigned pos = threadIdx.x; pos < total; pos += kStageThreads) {
+    for (unsigned pos = threadIdx.x; pos < total; pos += NT) {
         const unsigned o = b.order[pos];
         const unsigned d = o >> 16, e = o & 0xFFFFu;
         if (pos < b.ok_end[d]) {
@@ -153,7 +170,7 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
             for (int w = 0; w < W; ++w) out_rec[g * W + w] = b.stage[(size_t)e * W + w];
         }
     }
-    for (unsigned d = threadIdx.x; d < P; d += kStageThreads) b.hist[d] = 0;
+    for (unsigned d = threadIdx.x; d < P; d += NT) b.hist[d] = 0;
     if (over) atomicOr(status, overflow_bit);
     __syncthreads();
 }
