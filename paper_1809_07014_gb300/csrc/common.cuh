@@ -121,19 +121,20 @@ struct Geometry {
     __host__ __device__ unsigned zl_bits() const { return bt - ps - p1; }  // bits of z kept in the record
 };
 
-// z of a key.  One word (k <= 31): the key times an odd constant modulo
-// 2^(2k), a bijection whose top bits (the partition) depend on every key bit
-// through the carries.  Several words: the last word xored with a hash of
-// the head words, then mixed on 64 bits.
+// z of a key: a bijection of its last word times an odd constant modulo 2^bt,
+// whose top bits (the partition) depend on every bit through the carries.
+// One word (k <= 31, bt = 2k): the key itself.  Several words (bt = 64): the
+// last word xored with a hash of the head words, so that z depends on the
+// whole key.
 template <int W>
 __host__ __device__ inline unsigned long long key_to_z(const unsigned long long (&key)[W], unsigned bt) {
-    return W == 1 ? (key[0] * kM1) & low_mask(bt) : mix_bits(key[W - 1] ^ head_hash<W>(key), 64);
+    return W == 1 ? (key[0] * kM1) & low_mask(bt) : (key[W - 1] ^ head_hash<W>(key)) * kM1;
 }
 // Recover the key's last word from z and the head words.
 template <int W>
 __host__ __device__ inline unsigned long long z_to_tail(unsigned long long z, const unsigned long long (&key)[W],
                                                      unsigned bt) {
-    return W == 1 ? (z * kM1i) & low_mask(bt) : (unmix_bits(z, 64) ^ head_hash<W>(key));
+    return W == 1 ? (z * kM1i) & low_mask(bt) : ((z * kM1i) ^ head_hash<W>(key));
 }
 
 // ------------------------------------------------------- job description

@@ -11,7 +11,7 @@ constexpr unsigned kRepartThreads = 512;
 
 template <int W>
 struct RepartShape {
-    static constexpr unsigned S = W == 1 ? 4096 : (W == 2 ? 2048 : 1024);  // records per tile
+    static constexpr unsigned S = W == 1 ? 4096 : (W == 2 ? 3072 : 2048);  // records per tile
 };
 
 __host__ __device__ inline unsigned repart_tile(unsigned W) {

@@ -11,7 +11,8 @@ namespace kmer {
 
 template <int W>
 struct ScatterShape {
-    static constexpr unsigned R = W == 1 ? 16 : (W == 2 ? 8 : 4);  // read positions per round
+    // read positions per round: 4096 records (W = 1) or about 48 KB of records staged
+    static constexpr unsigned R = W == 1 ? 16 : (W == 2 ? 12 : (W == 3 ? 8 : 6));
     static constexpr unsigned S = R * kStageThreads;                 // staged records per round
 };
 
@@ -119,7 +120,9 @@ static cudaError_t launch_scatter_wp(const Job* jobs, const unsigned long long* 
 template <int W>
 static cudaError_t launch_scatter_w(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
                                     unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+    // MAXPER: destinations of one thread in a flush (fan-out / 256, rounded up to 2, 4 or 8)
     if ((1u << max_p1) <= 2 * kStageThreads) return launch_scatter_wp<W, 2>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+    if ((1u << max_p1) <= 4 * kStageThreads) return launch_scatter_wp<W, 4>(jobs, tile_off, n_jobs, tiles, max_p1, s);
     return launch_scatter_wp<W, kMaxStageDest / kStageThreads>(jobs, tile_off, n_jobs, tiles, max_p1, s);
 }
 
