@@ -363,13 +363,12 @@ def run_ours(args):
         rset_h = pkg.ReadSet(b_h, q_h, o_h, stream=stream)
 
         def e2e_step():
+            # reads from pinned host buffers; survivors written straight into pinned host buffers
             rset_h.pack(b_h, q_h, o_h, stream=stream)
             ka.reset()
             ka.submit(rset_h)
-            vv = ka.query()
-            pkg.kmer_analysis_copy_results(ka.handle, keys_h.data_ptr(), cnt_h.data_ptr(), ext_h.data_ptr(),
-                                           cls_h.data_ptr(), cap)
-            return vv
+            return pkg.kmer_analysis_query_into(ka.handle, keys_h.data_ptr(), cnt_h.data_ptr(), ext_h.data_ptr(),
+                                                cls_h.data_ptr(), cap, pkg.KMER_HOST)
         vv = e2e_step()
         torch.cuda.synchronize()
         barrier()

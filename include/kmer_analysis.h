@@ -198,6 +198,18 @@ int kmer_analysis_submit_raw(kmer_analysis_t *h, const char *bases, const uint8_
  * TIMEOUT, CUDA; the previous results are invalid after an error. */
 int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
 
+/* As kmer_analysis_query, but the survivors are written straight into the
+ * caller's arrays (layouts as in kmer_result_view) as the kernels find them,
+ * instead of into the analysis's buffers: with page-locked host arrays
+ * (where = KMER_HOST) the transfer to the host overlaps the counting.  The
+ * arrays hold `capacity` k-mers and must not overlap; *out points at them.
+ * The results stay valid (for views, copies and lookups) until the next
+ * query, reset or destroy.  Errors: as kmer_analysis_query, plus
+ * INVALID_ARG for NULL arrays, host arrays that are not page-locked, or more
+ * survivors than `capacity` (kmer_last_error_message gives the count). */
+int kmer_analysis_query_into(kmer_analysis_t *h, uint64_t *keys, uint32_t *count, uint32_t *ext, uint8_t *cls,
+                             uint64_t capacity, int where, kmer_result_view *out);
+
 /* Copies the survivors of the last query to host memory: keys (n * W words),
  * count (n), ext (n * 8), cls (n * 2); any pointer may be NULL to skip that
  * array; `capacity` is the number of k-mers the buffers hold.  Synchronous.

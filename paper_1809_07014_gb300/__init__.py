@@ -123,6 +123,7 @@ _SIGNATURES = {
     "kmer_analysis_query": (_int, [_vp, ctypes.POINTER(kmer_result_view)]),
     "kmer_analysis_copy_results": (_int, [_vp, _vp, _vp, _vp, _vp, _u64]),
     "kmer_analysis_lookup": (_int, [_vp, _vp, _u64, _vp, _int]),
+    "kmer_analysis_query_into": (_int, [_vp, _vp, _vp, _vp, _vp, _u64, _int, ctypes.POINTER(kmer_result_view)]),
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
@@ -238,6 +239,14 @@ def kmer_analysis_query(h: int) -> kmer_result_view:
 KMER_RECORD_DTYPE = np.dtype([("count", "<u4"), ("ext", "<u4", (8,)), ("cls", "u1", (2,)), ("found", "u1"),
                               ("flipped", "u1")])
 assert KMER_RECORD_DTYPE.itemsize == 40
+
+
+def kmer_analysis_query_into(h: int, keys: int, count: int, ext: int, cls: int, capacity: int,
+                             where: int) -> kmer_result_view:
+    v = kmer_result_view()
+    _check(load_library().kmer_analysis_query_into(h, keys, count, ext, cls, capacity, where, ctypes.byref(v)),
+           "kmer_analysis_query_into")
+    return v
 
 
 def kmer_analysis_lookup(h: int, keys: int, n: int, out: int, where: int) -> None:

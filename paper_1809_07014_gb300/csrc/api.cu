@@ -165,6 +165,13 @@ struct kmer_analysis {
     DevBuf out_keys, out_count, out_ext, out_cls;
     DevBuf fb_list, split_list, hbm, misc;
     DevBuf lk_index, lk_keys, lk_out;  // survivors' index for lookups, staging of host lookups
+    // survivors written straight into caller buffers (kmer_analysis_query_into): device
+    // addresses of those buffers while such a query runs, and of the results after it
+    bool ext_out = false;
+    unsigned long long* res_keys = nullptr;
+    unsigned* res_count = nullptr;
+    unsigned* res_ext = nullptr;
+    unsigned char* res_cls = nullptr;
     unsigned long long lk_cap = 0;     // index slots; 0 = no index for the current results
     DevBuf d_ajob, d_sjobs, d_tile_off, d_leaf_off, d_job_tile_off;  // job descriptors and work maps
     unsigned long long out_cap = 0, fb_cap = 0;
@@ -378,6 +385,8 @@ int read_misc(kmer_analysis* h) {
 
 int ensure_output(kmer_analysis* h, unsigned long long cap, unsigned long long keep) {
     if (cap <= h->out_cap) return KMER_OK;
+    if (h->ext_out)  // the caller's buffers cannot grow
+        return fail(KMER_ERR_INVALID_ARG, "output capacity %llu < %llu survivors", h->out_cap, cap);
     const unsigned W = h->W();
     cap = std::max(cap, (unsigned long long)1024);
     DevBuf nk, nc, ne, ncl;
@@ -406,10 +415,16 @@ int ensure_output(kmer_analysis* h, unsigned long long cap, unsigned long long k
 
 void fill_job_outputs(kmer_analysis* h, Job& j) {
     Misc* m = h->misc.as<Misc>();
-    j.out_keys = h->out_keys.as<unsigned long long>();
-    j.out_count = h->out_count.as<unsigned int>();
-    j.out_ext = h->out_ext.as<unsigned int>();
-    j.out_cls = h->out_cls.as<unsigned char>();
+    if (!h->ext_out) {
+        h->res_keys = h->out_keys.as<unsigned long long>();
+        h->res_count = h->out_count.as<unsigned int>();
+        h->res_ext = h->out_ext.as<unsigned int>();
+        h->res_cls = h->out_cls.as<unsigned char>();
+    }
+    j.out_keys = h->res_keys;
+    j.out_count = h->res_count;
+    j.out_ext = h->res_ext;
+    j.out_cls = h->res_cls;
     j.out_cap = h->out_cap;
     j.out_n = &m->out_n;
     j.status = &m->status;
@@ -520,7 +535,7 @@ int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     }
     TRY(read_misc(h));
     const unsigned long long out_now = h->host_misc->out_n;
-    TRY(ensure_output(h, out_now + extra_out, out_now));
+    if (!h->ext_out) TRY(ensure_output(h, out_now + extra_out, out_now));
     fill_job_outputs(h, j);
     const unsigned W = j.g.W;
     const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * max_n));
@@ -715,7 +730,7 @@ int run_direct(kmer_analysis* h, unsigned long long windows) {
     g.bt = W == 1 ? 2 * g.k : 64;
     const unsigned long long basis = h->p.distinct_hint ? h->p.distinct_hint : windows;
     unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, basis + basis / 3));
-    TRY(ensure_output(h, std::min(windows / h->p.min_count + 1024, basis + 1024), 0));
+    if (!h->ext_out) TRY(ensure_output(h, std::min(windows / h->p.min_count + 1024, basis + 1024), 0));
     for (unsigned attempt = 0;; ++attempt) {
         TRY(h->hbm.ensure(cap * hbm_entry_bytes(W)));
         CK(cudaMemsetAsync(h->hbm.p, 0, cap * hbm_entry_bytes(W), h->stream));
@@ -782,9 +797,9 @@ int do_query(kmer_analysis* h) {
             const unsigned long long bound = windows / h->p.min_count + 1024;
             unsigned long long want = h->out_hint ? h->out_hint + h->out_hint / 16 + 4096 : windows / 4 + 4096;
             if (!h->out_hint) want = std::min<unsigned long long>(want, 0.35 * (double)budget / out_bytes_per + 4096);
-            TRY(ensure_output(h, std::min(bound, want), 0));
+            if (!h->ext_out) TRY(ensure_output(h, std::min(bound, want), 0));
             // the records of a pass get what the output leaves of the budget
-            const size_t out_bytes = (size_t)(h->out_cap * out_bytes_per);
+            const size_t out_bytes = h->ext_out ? 0 : (size_t)(h->out_cap * out_bytes_per);
             h->hint_ratio = h->p.distinct_hint ? std::min(1.0, (double)h->p.distinct_hint / (double)windows) : 0.0;
             const Plan pl = make_plan(h, windows, budget > 2 * out_bytes ? budget - out_bytes : budget / 2, cap_max);
             h->st.pass_bits = pl.g.ps;
@@ -962,10 +977,51 @@ int kmer_analysis_query(kmer_analysis_t* h, kmer_result_view* out) {
     out->n = h->n_out;
     out->k = h->p.k;
     out->words = h->W();
-    out->keys = h->out_keys.as<uint64_t>();
-    out->count = h->out_count.as<uint32_t>();
-    out->ext = h->out_ext.as<uint32_t>();
-    out->cls = h->out_cls.as<uint8_t>();
+    out->keys = reinterpret_cast<const uint64_t*>(h->res_keys);
+    out->count = h->res_count;
+    out->ext = h->res_ext;
+    out->cls = h->res_cls;
+    out->windows = h->res_windows;
+    out->distinct = h->res_distinct;
+    return KMER_OK;
+}
+
+int kmer_analysis_query_into(kmer_analysis_t* h, uint64_t* keys, uint32_t* count, uint32_t* ext, uint8_t* cls,
+                             uint64_t capacity, int where, kmer_result_view* out) {
+    if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
+    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (!keys || !count || !ext || !cls) return fail(KMER_ERR_INVALID_ARG, "every output array is required");
+    DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
+    std::memset(out, 0, sizeof *out);
+    void* ptrs[4] = {keys, count, ext, cls};
+    if (where == KMER_HOST)
+        for (auto& p : ptrs) {
+            p = const_cast<void*>(host_mapped(p));
+            if (!p) return fail(KMER_ERR_INVALID_ARG, "host output buffers must be page-locked");
+        }
+    const unsigned long long own_cap = h->out_cap;
+    h->ext_out = true;
+    h->res_keys = static_cast<unsigned long long*>(ptrs[0]);
+    h->res_count = static_cast<unsigned*>(ptrs[1]);
+    h->res_ext = static_cast<unsigned*>(ptrs[2]);
+    h->res_cls = static_cast<unsigned char*>(ptrs[3]);
+    h->out_cap = capacity;
+    const int rc = do_query(h);
+    h->ext_out = false;
+    h->out_cap = own_cap;
+    if (rc != KMER_OK) {
+        h->have_result = false;
+        cudaGetLastError();
+        return rc;
+    }
+    out->n = h->n_out;
+    out->k = h->p.k;
+    out->words = h->W();
+    out->keys = keys;
+    out->count = count;
+    out->ext = ext;
+    out->cls = cls;
     out->windows = h->res_windows;
     out->distinct = h->res_distinct;
     return KMER_OK;
@@ -980,10 +1036,10 @@ int kmer_analysis_copy_results(kmer_analysis_t* h, uint64_t* keys, uint32_t* cou
     DeviceGuard dg(h->device);
     const unsigned long long n = h->n_out;
     if (n) {
-        if (keys) CK(cudaMemcpyAsync(keys, h->out_keys.p, n * 8 * h->W(), cudaMemcpyDeviceToHost, h->stream));
-        if (count) CK(cudaMemcpyAsync(count, h->out_count.p, n * 4, cudaMemcpyDeviceToHost, h->stream));
-        if (ext) CK(cudaMemcpyAsync(ext, h->out_ext.p, n * 32, cudaMemcpyDeviceToHost, h->stream));
-        if (cls) CK(cudaMemcpyAsync(cls, h->out_cls.p, n * 2, cudaMemcpyDeviceToHost, h->stream));
+        if (keys) CK(cudaMemcpyAsync(keys, h->res_keys, n * 8 * h->W(), cudaMemcpyDefault, h->stream));
+        if (count) CK(cudaMemcpyAsync(count, h->res_count, n * 4, cudaMemcpyDefault, h->stream));
+        if (ext) CK(cudaMemcpyAsync(ext, h->res_ext, n * 32, cudaMemcpyDefault, h->stream));
+        if (cls) CK(cudaMemcpyAsync(cls, h->res_cls, n * 2, cudaMemcpyDefault, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
     return KMER_OK;
@@ -1003,7 +1059,7 @@ int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, k
         const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * h->n_out));
         TRY(h->lk_index.ensure(cap * 4));
         CK(cudaMemsetAsync(h->lk_index.p, 0xFF, cap * 4, h->stream));
-        CK(launch_index_build(W, h->out_keys.as<unsigned long long>(), h->n_out, h->lk_index.as<unsigned>(), cap,
+        CK(launch_index_build(W, h->res_keys, h->n_out, h->lk_index.as<unsigned>(), cap,
                               h->num_sms, h->stream));
         h->lk_cap = cap;
     }
@@ -1016,8 +1072,8 @@ int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, k
         dq = h->lk_keys.as<unsigned long long>();
         dout = h->lk_out.as<kmer_record>();
     }
-    CK(launch_lookup(W, dq, n, h->p.k, h->lk_index.as<unsigned>(), h->lk_cap, h->out_keys.as<unsigned long long>(),
-                     h->out_count.as<unsigned>(), h->out_ext.as<unsigned>(), h->out_cls.as<unsigned char>(), dout,
+    CK(launch_lookup(W, dq, n, h->p.k, h->lk_index.as<unsigned>(), h->lk_cap, h->res_keys, h->res_count, h->res_ext,
+                     h->res_cls, dout,
                      h->num_sms, h->stream));
     if (where == KMER_HOST)
         CK(cudaMemcpyAsync(out, dout, n * sizeof(kmer_record), cudaMemcpyDeviceToHost, h->stream));

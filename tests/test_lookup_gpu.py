@@ -98,3 +98,53 @@ def test_lookup_rejects_before_a_query_and_reuses_its_index(sample):
     assert not ka.lookup(bad)["found"].any()
     ka.close()
     rs.close()
+
+
+def test_query_into_caller_buffers(sample):
+    """Survivors written straight into caller arrays: page-locked host memory
+    or device memory give the regular query's results; a too small capacity
+    or pageable host memory is refused."""
+    import torch
+    rs = pkg.ReadSet(sample.bases, sample.quals, sample.offsets)
+    for k in (31, 55):
+        ka = pkg.KmerAnalysis(k)
+        ka.submit(rs)
+        ref = ka.results()
+        n, W = len(ref), (2 * k + 63) // 64
+        for where, dev in ((pkg.KMER_HOST, None), (pkg.KMER_DEVICE, "cuda")):
+            mk = (lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()) if dev is None else \
+                 (lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda"))
+            cap = n + 17
+            keys, cnt = mk((cap, W), torch.int64), mk(cap, torch.int32)
+            ext, cls = mk((cap, 8), torch.int32), mk((cap, 2), torch.uint8)
+            ka.reset()
+            ka.submit(rs)
+            v = pkg.kmer_analysis_query_into(ka.handle, keys.data_ptr(), cnt.data_ptr(), ext.data_ptr(),
+                                             cls.data_ptr(), cap, where)
+            assert int(v.n) == n and int(v.windows) == ref.windows and int(v.distinct) == ref.distinct
+            got = pkg.Result(k, keys[:n].cpu().numpy().view(np.uint64), cnt[:n].cpu().numpy().view(np.uint32),
+                             ext[:n].cpu().numpy().view(np.uint32), cls[:n].cpu().numpy(), ref.windows, ref.distinct)
+            from tests.test_batch_gpu import same_result
+            same_result(got, ref)
+            # lookups and copies read the caller's arrays
+            rec = ka.lookup(ref.keys[:50])
+            assert rec["found"].all() and np.array_equal(rec["count"], ref.count[:50])
+        # too small a capacity, and pageable host memory, are refused
+        small = [torch.empty((max(1, n // 2), W), dtype=torch.int64).pin_memory(),
+                 torch.empty(max(1, n // 2), dtype=torch.int32).pin_memory(),
+                 torch.empty((max(1, n // 2), 8), dtype=torch.int32).pin_memory(),
+                 torch.empty((max(1, n // 2), 2), dtype=torch.uint8).pin_memory()]
+        ka.reset()
+        ka.submit(rs)
+        with pytest.raises(pkg.KmerError) as e:
+            pkg.kmer_analysis_query_into(ka.handle, *[t.data_ptr() for t in small], max(1, n // 2), pkg.KMER_HOST)
+        assert e.value.code == pkg.KMER_ERR_INVALID_ARG
+        pageable = [np.empty((n, W), np.uint64), np.empty(n, np.uint32), np.empty((n, 8), np.uint32),
+                    np.empty((n, 2), np.uint8)]
+        ka.reset()
+        ka.submit(rs)
+        with pytest.raises(pkg.KmerError) as e:
+            pkg.kmer_analysis_query_into(ka.handle, *[a.ctypes.data for a in pageable], n, pkg.KMER_HOST)
+        assert e.value.code == pkg.KMER_ERR_INVALID_ARG
+        ka.close()
+    rs.close()
