@@ -259,9 +259,9 @@ int kmer_analysis_destroy(kmer_analysis_t *h);
  * output or leaf layout turns out too small is repaired inside its wave (the
  * stages after the scatter re-run for that job); a job whose level-1 buckets
  * overflow, or that is too large for any wave, is re-run alone through the
- * regular path.  Results are always exact.  A run whose counts differ much
- * from what a job was planned for (distinct keys off by more than 25% down
- * or 40% up) teaches the batch: the next run re-plans with those counts and
+ * regular path.  Results are always exact.  A run whose counts differ from
+ * what a job was planned for (distinct keys more than 10% above or 25% below
+ * the plan) teaches the batch: the next run re-plans with those counts and
  * re-captures the graphs. */
 typedef struct kmer_batch kmer_batch_t;
 

@@ -627,7 +627,7 @@ int run_batch(kmer_batch* b) {
         // a job with a learned exact leaf layout keeps its plan
         if (j.windows == 0 || j.used_alone || !good[i] || j.l2_exact.p) continue;
         const double r = (double)j.res_distinct / (double)j.basis;
-        if (r > 1.25 || r < 0.6) {
+        if (r > 1.1 || r < 0.75) {
             if (j.p.leaf_bits) {
                 const double per_leaf = (double)j.basis / (double)(1ull << j.p.leaf_bits);
                 unsigned lb = ceil_log2((unsigned long long)std::max(2.0, (double)j.res_distinct / per_leaf));

@@ -67,36 +67,8 @@ __host__ __device__ inline unsigned long long low_mask(unsigned b) {
     return b >= 64 ? ~0ull : ((1ull << b) - 1ull);
 }
 
-// Inverse of x ^= x >> s on b-bit values.
-__host__ __device__ inline unsigned long long unxorshift(unsigned long long y, unsigned s) {
-    unsigned long long x = y;
-    for (unsigned t = s; t < 64; t += s) x ^= y >> t;
-    return x;
-}
-
-// A bijection on b-bit integers (2 <= b <= 64): xorshift, multiply by an odd
-// constant mod 2^b, xorshift -- each step invertible on b bits.  The top bits
-// of z (partition) depend on every key bit through the multiply's carries;
-// the final xorshift folds them back into the low bits (table slot).
-__host__ __device__ inline unsigned long long mix_bits(unsigned long long x, unsigned b) {
-    const unsigned long long m = low_mask(b);
-    const unsigned s = b > 2 ? (b + 1) / 2 : 1;
-    x ^= x >> s;
-    x = (x * kM1) & m;
-    x ^= x >> s;
-    return x;
-}
-__host__ __device__ inline unsigned long long unmix_bits(unsigned long long z, unsigned b) {
-    const unsigned long long m = low_mask(b);
-    const unsigned s = b > 2 ? (b + 1) / 2 : 1;
-    z = unxorshift(z, s) & m;
-    z = (z * kM1i) & m;
-    z = unxorshift(z, s) & m;
-    return z;
-}
-
-// Hash of the head words (words 0..W-2) that is xored into the tail before
-// mixing, so that z depends on the whole key.
+// Hash of the head words (words 0..W-2) that is xored into the last word
+// before the multiply, so that z depends on the whole key.
 template <int W>
 __host__ __device__ inline unsigned long long head_hash(const unsigned long long (&w)[W]) {
     unsigned long long h = 0x9E3779B97F4A7C15ull;
