@@ -218,12 +218,18 @@ __global__ void __launch_bounds__(256) pack_kernel(const char* __restrict__ base
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const unsigned v = cb[i];
-                const unsigned eq = __vcmpeq4(v, 0x41414141u) | __vcmpeq4(v, 0x43434343u) |
-                                    __vcmpeq4(v, 0x47474747u) | __vcmpeq4(v, 0x54545454u);
                 // A, C, G, T (0x41, 0x43, 0x47, 0x54) -> 0, 1, 2, 3: bit 1 ^ bit 2, bit 2 ^ bit 3
-                const unsigned c2 = ((v >> 1) ^ (v >> 2)) & 0x03030303u & eq;
+                unsigned c2 = ((v >> 1) ^ (v >> 2)) & 0x03030303u;
+                // a byte is a base iff it equals the letter of its code: one byte
+                // permutation looks up the four letters, an exact zero-byte test compares
+                const unsigned x = c2 | (c2 >> 4);
+                const unsigned letters = __byte_perm(0x54474341u, 0u, (x & 0xFFu) | ((x >> 8) & 0xFF00u));
+                const unsigned t = v ^ letters;
+                const unsigned ok = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);  // 0x80 per base byte
+                const unsigned eq = (ok >> 7) * 0xFFu;  // 0xFF per base byte
+                c2 &= eq;
                 codes |= (unsigned long long)((c2 * 0x01041040u) >> 24) << (8 * i);
-                valid |= byte_lsbs(eq) << (4 * i);
+                valid |= byte_lsbs(ok >> 7) << (4 * i);
                 hq |= byte_lsbs(__vcmpgeu4(cq[i], thr4) & eq) << (4 * i);
             }
             if (hq_never) hq = 0u;
