@@ -171,19 +171,19 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
         const unsigned P2 = 1u << j.g.p2;
         const unsigned zb = j.g.zl_bits();
         const unsigned shift = zb - j.g.p2;
+        unsigned m[U];
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
             const unsigned e = u * kRepartThreads + threadIdx.x;
-            unsigned m = 0xFFFFFFFFu;
+            m[u] = 0xFFFFFFFFu;
             if (e < rt.cnt) {
                 const unsigned long long zl = rec[u][W - 1] >> 6;
                 const unsigned sub = (unsigned)(zl >> shift) & (P2 - 1u);
                 const unsigned rank = atomicAdd(&b.hist[sub], 1u);
 #pragma unroll
                 for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[u][w];
-                m = (sub << 16) | rank;
+                m[u] = (sub << 16) | rank;
             }
-            b.meta[e] = m;
         }
         // the next tile's loads are in flight during this tile's flush
         const unsigned long long ngt = gt + gridDim.x;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
             load(nrt);
         }
         L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[rt.bucket], j.l2_leafcap[rt.bucket], rt.bucket << j.g.p2};
-        flush_stage<W, MAXPER, L2Dest, kRepartThreads>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW);
+        flush_stage_regs<W, MAXPER, L2Dest, kRepartThreads, U>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW, m);
         gt = ngt;
         rt = nrt;
     }

@@ -109,9 +109,13 @@ __device__ inline StageBufs carve_stage(unsigned char* base, unsigned W, unsigne
 // says which staged record goes there and to which destination, and
 // consecutive threads write consecutive positions, i.e. contiguous runs per
 // destination.
-template <int W, unsigned MAXPER, class Dest, unsigned NT = kStageThreads>
-__device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
-                            unsigned* status, unsigned overflow_bit) {
+//
+// `sort` places every staged record's word in `order` once the local bases
+// are known (from meta[] in shared memory, or from registers).
+template <int W, unsigned MAXPER, class Dest, unsigned NT, class Sort>
+__device__ __forceinline__ void flush_stage_with(const StageBufs& b, unsigned S, unsigned P, Dest& dest,
+                                                 unsigned long long* out_rec, unsigned* status,
+                                                 unsigned overflow_bit, Sort sort) {
     __syncthreads();
     // exclusive scan of hist -> lbase (each thread owns a run of consecutive destinations)
     const unsigned per = (P + NT - 1) / NT;
@@ -140,10 +144,7 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
         }
     }
     __syncthreads();
-    for (unsigned e = threadIdx.x; e < S; e += NT) {
-        const unsigned m = b.meta[e];
-        if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (m & 0xFFFF0000u) | e;
-    }
+    sort();
     bool over = false;
     run = run0;
 #pragma unroll
@@ -173,6 +174,30 @@ __device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& de
     for (unsigned d = threadIdx.x; d < P; d += NT) b.hist[d] = 0;
     if (over) atomicOr(status, overflow_bit);
     __syncthreads();
+}
+
+// Sorted position of staged record e with meta word m (see flush_stage).
+__device__ __forceinline__ void place(const StageBufs& b, unsigned m, unsigned e) {
+    if (m != 0xFFFFFFFFu) b.order[b.lbase[m >> 16] + (m & 0xFFFFu)] = (m & 0xFFFF0000u) | e;
+}
+
+// Meta words in shared memory (meta[e] for every staged record e).
+template <int W, unsigned MAXPER, class Dest, unsigned NT = kStageThreads>
+__device__ void flush_stage(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
+                            unsigned* status, unsigned overflow_bit) {
+    flush_stage_with<W, MAXPER, Dest, NT>(b, S, P, dest, out_rec, status, overflow_bit, [&]() {
+        for (unsigned e = threadIdx.x; e < S; e += NT) place(b, b.meta[e], e);
+    });
+}
+
+// Meta words in registers: m[u] belongs to staged record u * NT + threadIdx.x.
+template <int W, unsigned MAXPER, class Dest, unsigned NT, unsigned U>
+__device__ void flush_stage_regs(const StageBufs& b, unsigned S, unsigned P, Dest& dest, unsigned long long* out_rec,
+                                 unsigned* status, unsigned overflow_bit, const unsigned (&m)[U]) {
+    flush_stage_with<W, MAXPER, Dest, NT>(b, S, P, dest, out_rec, status, overflow_bit, [&]() {
+#pragma unroll
+        for (unsigned u = 0; u < U; ++u) place(b, m[u], u * NT + threadIdx.x);
+    });
 }
 
 }  // namespace kmer
