@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--large", action="store_true",
                     help="serve: also run the 15-Gbase, 500-genome instance at k=55 within a 180 GB budget")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-threads", type=int, default=2, help="host threads of the end-to-end pipeline")
+    ap.add_argument("--e2e-io", choices=["staged", "in-place"], default="in-place",
+                    help="end to end with several threads: host buffers moved by the copy engines "
+                         "(KMER_HOST_STAGED) or read and written in place by the kernels (KMER_HOST)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -352,10 +356,10 @@ def run_ours(args):
 
     # ---- end to end through the C ABI from pinned host buffers: every step packs
     # its reads from pinned host memory and writes its survivors into pinned
-    # host memory.  Two host threads, each with its own readset, analysis and
-    # stream, take alternate steps, so one step's reads cross the host link
-    # while the other step counts and writes its results back; the
-    # single-thread figure is reported beside.
+    # host memory (in place by the kernels, or moved by the copy engines with
+    # --e2e-io staged).  Several host threads, each with its own readset,
+    # analysis and stream, take turns; the single-thread figure (in place) is
+    # reported beside.
     if not args.no_e2e:
         import threading
         ka.close()  # its device buffers go back to the pool for the two lanes below
@@ -363,8 +367,10 @@ def run_ours(args):
         q_h = torch.from_numpy(rs.quals).pin_memory()
         o_h = torch.from_numpy(rs.offsets.view(np.int64)).pin_memory()
         cap = n_surv + n_surv // 8 + 1024
+        n_thr = max(1, args.e2e_threads)
+        staged = args.e2e_io == "staged"
         lanes = []
-        for li in range(2):
+        for li in range(n_thr):
             st_l = torch.cuda.Stream(device=dev)
             lanes.append({
                 "stream": st_l,
@@ -376,38 +382,41 @@ def run_ours(args):
                 "ka": pkg.KmerAnalysis(args.k, stream=st_l, variant=variant, leaf_bits=args.leaf_bits),
                 "windows": 0, "d2h": 0})
 
-        def e2e_step(ln):
-            # reads from pinned host buffers; survivors written straight into pinned host buffers
-            ln["rs"].pack(b_h, q_h, o_h, stream=ln["stream"])
+        def e2e_step(ln, stg):
+            # reads from pinned host buffers; survivors into pinned host buffers
+            ln["rs"].pack(b_h, q_h, o_h, stream=ln["stream"], staged=stg)
             ln["ka"].reset()
             ln["ka"].submit(ln["rs"])
             vv = pkg.kmer_analysis_query_into(ln["ka"].handle, ln["keys"].data_ptr(), ln["cnt"].data_ptr(),
-                                              ln["ext"].data_ptr(), ln["cls"].data_ptr(), cap, pkg.KMER_HOST)
+                                              ln["ext"].data_ptr(), ln["cls"].data_ptr(), cap,
+                                              pkg.KMER_HOST_STAGED if stg else pkg.KMER_HOST)
             ln["windows"] += int(vv.windows)
             ln["d2h"] += int(vv.n) * (8 * W + 4 + 32 + 2)
 
-        def run_lane(ln, n):
+        def run_lane(ln, n, stg):
             torch.cuda.set_device(dev)
             for _ in range(n):
-                e2e_step(ln)
+                e2e_step(ln, stg)
 
         for ln in lanes:  # warm-up: allocations and learned sizing
-            e2e_step(ln)
-            e2e_step(ln)
+            e2e_step(ln, staged)
+            e2e_step(ln, staged)
+        e2e_step(lanes[0], False)
         torch.cuda.synchronize()
-        # one thread, one step at a time
+        # one thread, one step at a time, buffers read and written in place
         lanes[0]["windows"] = lanes[0]["d2h"] = 0
         barrier()
         t0 = time.perf_counter()
-        run_lane(lanes[0], args.steps)
+        run_lane(lanes[0], args.steps, False)
         torch.cuda.synchronize()
         dt1, w1 = reduce_over_ranks(time.perf_counter() - t0, lanes[0]["windows"], dev)
-        # two threads, alternate steps
+        # several threads taking turns
         for ln in lanes:
             ln["windows"] = ln["d2h"] = 0
         barrier()
         t0 = time.perf_counter()
-        ths = [threading.Thread(target=run_lane, args=(lanes[i], (args.steps + 1 - i) // 2)) for i in range(2)]
+        ths = [threading.Thread(target=run_lane, args=(lanes[i], (args.steps + n_thr - 1 - i) // n_thr, staged))
+               for i in range(n_thr)]
         for th in ths:
             th.start()
         for th in ths:
@@ -418,8 +427,10 @@ def run_ours(args):
         h2d = 2 * n_bases + 8 * (n_reads + 1)
         line["e2e"] = {"value": w2 / dt2, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": sum(ln["d2h"] for ln in lanes) // args.steps,
-                       "ms_per_step": 1e3 * dt2 / args.steps, "host_threads": 2,
-                       "one_thread": {"value": w1 / dt1, "ms_per_step": 1e3 * dt1 / args.steps}}
+                       "ms_per_step": 1e3 * dt2 / args.steps, "host_threads": n_thr,
+                       "host_io": "KMER_HOST_STAGED (copy engines)" if staged else "KMER_HOST (in place)",
+                       "one_thread": {"value": w1 / dt1, "ms_per_step": 1e3 * dt1 / args.steps,
+                                      "host_io": "KMER_HOST (in place)"}}
         for ln in lanes:
             ln["ka"].close()
             ln["rs"].close()

@@ -69,7 +69,14 @@ extern "C" {
 
 #define KMER_MAX_K 127
 
-enum kmer_where { KMER_HOST = 0, KMER_DEVICE = 1 };
+/* Where a buffer lives.  KMER_HOST_STAGED is host memory that moves
+ * through device buffers by the copy engines (cudaMemcpyAsync, in 64 MB
+ * pieces) instead of being read or written in place by the kernels: the
+ * kernels then touch only HBM, and the SMs are not held while the transfer
+ * runs.  KMER_HOST reads and writes page-locked memory in place, which
+ * overlaps the transfer with the kernels that make it; other host memory is
+ * staged in both modes. */
+enum kmer_where { KMER_HOST = 0, KMER_DEVICE = 1, KMER_HOST_STAGED = 2 };
 enum kmer_ext_mode { KMER_EXT_DEPTH_ADAPTIVE = 0, KMER_EXT_STATIC = 1 };
 enum kmer_class { KMER_CLS_A = 0, KMER_CLS_C = 1, KMER_CLS_G = 2, KMER_CLS_T = 3,
                   KMER_CLS_FORK = 4, KMER_CLS_DEAD_END = 5 };
@@ -149,8 +156,10 @@ void kmer_analysis_default_params(kmer_analysis_params *p, uint32_t k);
  * bases[offsets[i] .. offsets[i+1]) with one quality byte per base in quals
  * (same indexing); offsets has n_reads + 1 non-decreasing entries, offsets[0]
  * is normally 0, and every read is shorter than 2^31 bases.  `where` says
- * whether bases, quals and offsets are host (KMER_HOST, any host memory;
- * pinned memory copies fastest) or device (KMER_DEVICE) pointers.  The
+ * whether bases, quals and offsets are host (KMER_HOST, any host memory:
+ * page-locked memory is read in place by the pack kernel, other memory is
+ * staged; KMER_HOST_STAGED: always staged by the copy engines) or device
+ * (KMER_DEVICE) pointers.  The
  * quality test (Phred >= qual_threshold, Phred = byte - qual_offset) is
  * applied here, so every analysis that submits this readset must use the
  * same two values.  The caller keeps ownership of its buffers; they may be
@@ -201,7 +210,10 @@ int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
 /* As kmer_analysis_query, but the survivors are written straight into the
  * caller's arrays (layouts as in kmer_result_view) as the kernels find them,
  * instead of into the analysis's buffers: with page-locked host arrays
- * (where = KMER_HOST) the transfer to the host overlaps the counting.  The
+ * (where = KMER_HOST) the transfer to the host overlaps the counting.  With
+ * where = KMER_HOST_STAGED (any host arrays) the survivors go to the
+ * analysis's own device buffers first and are then copied to the arrays by
+ * the copy engines.  The
  * arrays hold `capacity` k-mers and must not overlap; *out points at them.
  * The results stay valid (for views, copies and lookups) until the next
  * query, reset or destroy.  Errors: as kmer_analysis_query, plus
@@ -232,7 +244,8 @@ typedef struct {
  * above 2k zero (a key with such bits is reported not found); either
  * orientation (a k-mer and its reverse complement are one vertex, Sec.
  * II-B).  One record per key is written to out.  keys and out are both host
- * memory (where = KMER_HOST) or both device memory (KMER_DEVICE).  The first
+ * memory (where = KMER_HOST or KMER_HOST_STAGED, both staged) or both
+ * device memory (KMER_DEVICE).  The first
  * lookup after a query builds an index of the survivors in device memory
  * (4 bytes per slot, 2-4 slots per survivor); later lookups reuse it.
  * Synchronous.  Errors: BAD_STATE (no successful query), INVALID_ARG (NULL

@@ -31,7 +31,7 @@ KMER_ERR_TIMEOUT = -5
 KMER_ERR_CUDA = -6
 KMER_ERR_BAD_STATE = -7
 KMER_ERR_NO_DEVICE = -8
-KMER_HOST, KMER_DEVICE = 0, 1
+KMER_HOST, KMER_DEVICE, KMER_HOST_STAGED = 0, 1, 2
 KMER_EXT_DEPTH_ADAPTIVE, KMER_EXT_STATIC = 0, 1
 KMER_VARIANT_PARTITIONED, KMER_VARIANT_HBM_TABLE = 0, 1
 KMER_CLS_FORK, KMER_CLS_DEAD_END = 4, 5
@@ -382,8 +382,10 @@ def _ptr(a) -> int:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-def _where(a) -> int:
-    return KMER_DEVICE if (hasattr(a, "is_cuda") and a.is_cuda) else KMER_HOST
+def _where(a, staged: bool = False) -> int:
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        return KMER_DEVICE
+    return KMER_HOST_STAGED if staged else KMER_HOST
 
 
 def _stream_of(stream) -> int:
@@ -406,9 +408,12 @@ def make_params(k: int, **kw) -> kmer_analysis_params:
 class ReadSet:
     """Packed reads resident on the GPU (step a1)."""
 
-    def __init__(self, bases, quals, offsets, qual_offset: int = 33, qual_threshold: int = 20, stream=None):
-        where = _where(bases)
-        if _where(quals) != where or _where(offsets) != where:
+    def __init__(self, bases, quals, offsets, qual_offset: int = 33, qual_threshold: int = 20, stream=None,
+                 staged: bool = False):
+        """staged: host reads are copied to the device by the copy engines
+        (KMER_HOST_STAGED) even when page-locked, instead of read in place."""
+        where = _where(bases, staged)
+        if _where(quals, staged) != where or _where(offsets, staged) != where:
             raise ValueError("bases, quals and offsets must all be on the host or all on the device")
         n = len(offsets) - 1
         if n < 0:
@@ -417,10 +422,10 @@ class ReadSet:
                                           qual_threshold, where, _stream_of(stream))
         self.qual_offset, self.qual_threshold = qual_offset, qual_threshold
 
-    def pack(self, bases, quals, offsets, stream=None):
+    def pack(self, bases, quals, offsets, stream=None, staged: bool = False):
         """Re-pack new reads into this readset, reusing its device buffers."""
         kmer_readset_pack(self.handle, _ptr(bases), _ptr(quals), _ptr(offsets), len(offsets) - 1,
-                          _where(bases), _stream_of(stream))
+                          _where(bases, staged), _stream_of(stream))
 
     @property
     def launches(self) -> int:

@@ -225,6 +225,8 @@ int validate_params(const kmer_analysis_params* p) {
     return KMER_OK;
 }
 
+bool valid_where(int where) { return where == KMER_HOST || where == KMER_DEVICE || where == KMER_HOST_STAGED; }
+
 // Device address of page-locked host memory, or null for any other pointer.
 const void* host_mapped(const void* p) {
     cudaPointerAttributes a{};
@@ -233,6 +235,28 @@ const void* host_mapped(const void* p) {
         return nullptr;
     }
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// A large host<->device copy in 64 MB pieces with at most two in flight
+// (the calling thread waits).  Copies in one direction share a copy engine in
+// submission order: a small copy that another stream submits (counters,
+// descriptors) then waits for one piece, not for the whole transfer.
+cudaError_t paced_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    constexpr size_t kPiece = 64ull << 20;
+    if (bytes <= 2 * kPiece) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    for (size_t off = 0, k = 0; e == cudaSuccess && off < bytes; off += kPiece, ++k) {
+        if (k >= 2) e = cudaEventSynchronize(ev[k & 1]);
+        if (e != cudaSuccess) break;
+        const size_t n = bytes - off < kPiece ? bytes - off : kPiece;
+        e = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, n, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k & 1], s);
+    }
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    return e;
 }
 
 int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
@@ -246,13 +270,15 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
     const char* d_bases = bases;
     const uint8_t* d_quals = quals;
     TRY(rs->offsets.ensure((n_reads + 1) * 8));
-    if (where == KMER_HOST) {
+    if (where != KMER_DEVICE) {
         // offsets are checked on the device (read_geometry_kernel)
         CK(cudaMemcpyAsync(rs->offsets.p, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
         // page-locked host memory is read in place by the pack kernel over the
-        // host link (one pass, no staging copy); other host memory is staged
-        const char* mb = static_cast<const char*>(host_mapped(bases));
-        const uint8_t* mq = static_cast<const uint8_t*>(host_mapped(quals));
+        // host link (one pass, no staging copy) unless staging is asked for;
+        // other host memory is staged
+        const bool in_place = where == KMER_HOST;
+        const char* mb = in_place ? static_cast<const char*>(host_mapped(bases)) : nullptr;
+        const uint8_t* mq = in_place ? static_cast<const uint8_t*>(host_mapped(quals)) : nullptr;
         if (mb && mq) {
             d_bases = mb;
             d_quals = mq;
@@ -260,8 +286,8 @@ int pack_readset(kmer_readset* rs, const char* bases, const uint8_t* quals, cons
             const unsigned long long nb = offsets[n_reads];
             TRY(rs->tmp_bases.ensure(nb + 16));
             TRY(rs->tmp_quals.ensure(nb + 16));
-            CK(cudaMemcpyAsync(rs->tmp_bases.p, bases, nb, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(rs->tmp_quals.p, quals, nb, cudaMemcpyHostToDevice, s));
+            CK(paced_copy(rs->tmp_bases.p, bases, nb, s));
+            CK(paced_copy(rs->tmp_quals.p, quals, nb, s));
             d_bases = rs->tmp_bases.as<char>();
             d_quals = rs->tmp_quals.as<uint8_t>();
         }
@@ -324,7 +350,7 @@ int make_readset(const char* bases, const uint8_t* quals, const uint64_t* offset
                  uint32_t qual_offset, uint32_t qual_threshold, int where, cudaStream_t s, kmer_readset** out) {
     if (!out) return fail(KMER_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (!valid_where(where)) return fail(KMER_ERR_INVALID_ARG, "where must be HOST, DEVICE or HOST_STAGED");
     if (n_reads && (!bases || !quals || !offsets))
         return fail(KMER_ERR_INVALID_ARG, "bases, quals and offsets must be non-NULL when n_reads > 0");
     if (qual_offset > 255 || qual_threshold > 255)
@@ -870,7 +896,7 @@ int kmer_readset_create(const char* bases, const uint8_t* quals, const uint64_t*
 int kmer_readset_pack(kmer_readset_t* rs, const char* bases, const uint8_t* quals, const uint64_t* offsets,
                       uint64_t n_reads, int where, void* cuda_stream) {
     if (!rs) return fail(KMER_ERR_INVALID_ARG, "readset is NULL");
-    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (!valid_where(where)) return fail(KMER_ERR_INVALID_ARG, "where must be HOST, DEVICE or HOST_STAGED");
     if (n_reads && (!bases || !quals || !offsets))
         return fail(KMER_ERR_INVALID_ARG, "bases, quals and offsets must be non-NULL when n_reads > 0");
     DeviceGuard dg(rs->device);
@@ -989,11 +1015,40 @@ int kmer_analysis_query(kmer_analysis_t* h, kmer_result_view* out) {
 int kmer_analysis_query_into(kmer_analysis_t* h, uint64_t* keys, uint32_t* count, uint32_t* ext, uint8_t* cls,
                              uint64_t capacity, int where, kmer_result_view* out) {
     if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
-    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (!valid_where(where)) return fail(KMER_ERR_INVALID_ARG, "where must be HOST, DEVICE or HOST_STAGED");
     if (!keys || !count || !ext || !cls) return fail(KMER_ERR_INVALID_ARG, "every output array is required");
     DeviceGuard dg(h->device);
     StreamScope scope(h->stream);
     std::memset(out, 0, sizeof *out);
+    if (where == KMER_HOST_STAGED) {  // own device buffers, then the copy engines
+        const int rc = do_query(h);
+        if (rc != KMER_OK) {
+            h->have_result = false;
+            cudaGetLastError();
+            return rc;
+        }
+        if (h->n_out > capacity)
+            return fail(KMER_ERR_INVALID_ARG, "%llu survivors do not fit capacity %llu", h->n_out,
+                        (unsigned long long)capacity);
+        const unsigned long long n = h->n_out;
+        if (n) {
+            CK(paced_copy(keys, h->res_keys, n * 8 * h->W(), h->stream));
+            CK(paced_copy(count, h->res_count, n * 4, h->stream));
+            CK(paced_copy(ext, h->res_ext, n * 32, h->stream));
+            CK(paced_copy(cls, h->res_cls, n * 2, h->stream));
+        }
+        CK(cudaStreamSynchronize(h->stream));
+        out->n = n;
+        out->k = h->p.k;
+        out->words = h->W();
+        out->keys = keys;
+        out->count = count;
+        out->ext = ext;
+        out->cls = cls;
+        out->windows = h->res_windows;
+        out->distinct = h->res_distinct;
+        return KMER_OK;
+    }
     void* ptrs[4] = {keys, count, ext, cls};
     if (where == KMER_HOST)
         for (auto& p : ptrs) {
@@ -1036,10 +1091,10 @@ int kmer_analysis_copy_results(kmer_analysis_t* h, uint64_t* keys, uint32_t* cou
     DeviceGuard dg(h->device);
     const unsigned long long n = h->n_out;
     if (n) {
-        if (keys) CK(cudaMemcpyAsync(keys, h->res_keys, n * 8 * h->W(), cudaMemcpyDefault, h->stream));
-        if (count) CK(cudaMemcpyAsync(count, h->res_count, n * 4, cudaMemcpyDefault, h->stream));
-        if (ext) CK(cudaMemcpyAsync(ext, h->res_ext, n * 32, cudaMemcpyDefault, h->stream));
-        if (cls) CK(cudaMemcpyAsync(cls, h->res_cls, n * 2, cudaMemcpyDefault, h->stream));
+        if (keys) CK(paced_copy(keys, h->res_keys, n * 8 * h->W(), h->stream));
+        if (count) CK(paced_copy(count, h->res_count, n * 4, h->stream));
+        if (ext) CK(paced_copy(ext, h->res_ext, n * 32, h->stream));
+        if (cls) CK(paced_copy(cls, h->res_cls, n * 2, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
     return KMER_OK;
@@ -1047,7 +1102,7 @@ int kmer_analysis_copy_results(kmer_analysis_t* h, uint64_t* keys, uint32_t* cou
 
 int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, kmer_record* out, int where) {
     if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
-    if (where != KMER_HOST && where != KMER_DEVICE) return fail(KMER_ERR_INVALID_ARG, "where must be HOST or DEVICE");
+    if (!valid_where(where)) return fail(KMER_ERR_INVALID_ARG, "where must be HOST, DEVICE or HOST_STAGED");
     if (n && (!keys || !out)) return fail(KMER_ERR_INVALID_ARG, "keys and out must be non-NULL when n > 0");
     if (!h->have_result) return fail(KMER_ERR_BAD_STATE, "no successful query to look up in");
     if (h->n_out >= 0xFFFFFFFFull) return fail(KMER_ERR_INVALID_ARG, "index limited to 2^32 - 2 survivors");
@@ -1065,6 +1120,7 @@ int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, k
     }
     const unsigned long long* dq = reinterpret_cast<const unsigned long long*>(keys);
     kmer_record* dout = out;
+    if (where == KMER_HOST_STAGED) where = KMER_HOST;  // host arrays are always staged here
     if (where == KMER_HOST) {
         TRY(h->lk_keys.ensure(n * 8 * W));
         TRY(h->lk_out.ensure(n * sizeof(kmer_record)));

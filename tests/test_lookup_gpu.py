@@ -102,8 +102,9 @@ def test_lookup_rejects_before_a_query_and_reuses_its_index(sample):
 
 def test_query_into_caller_buffers(sample):
     """Survivors written straight into caller arrays: page-locked host memory
-    or device memory give the regular query's results; a too small capacity
-    or pageable host memory is refused."""
+    or device memory give the regular query's results, and so do pageable
+    host arrays filled by the copy engines (KMER_HOST_STAGED); a too small
+    capacity, or pageable host memory to be written in place, is refused."""
     import torch
     rs = pkg.ReadSet(sample.bases, sample.quals, sample.offsets)
     for k in (31, 55):
@@ -111,9 +112,14 @@ def test_query_into_caller_buffers(sample):
         ka.submit(rs)
         ref = ka.results()
         n, W = len(ref), (2 * k + 63) // 64
-        for where, dev in ((pkg.KMER_HOST, None), (pkg.KMER_DEVICE, "cuda")):
-            mk = (lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()) if dev is None else \
-                 (lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda"))
+        for where, dev in ((pkg.KMER_HOST, None), (pkg.KMER_DEVICE, "cuda"), (pkg.KMER_HOST_STAGED, "pageable"),
+                           (pkg.KMER_HOST_STAGED, None)):
+            if dev is None:
+                mk = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+            elif dev == "pageable":
+                mk = lambda shape, dt: torch.empty(shape, dtype=dt)
+            else:
+                mk = lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda")
             cap = n + 17
             keys, cnt = mk((cap, W), torch.int64), mk(cap, torch.int32)
             ext, cls = mk((cap, 8), torch.int32), mk((cap, 2), torch.uint8)
@@ -134,11 +140,12 @@ def test_query_into_caller_buffers(sample):
                  torch.empty(max(1, n // 2), dtype=torch.int32).pin_memory(),
                  torch.empty((max(1, n // 2), 8), dtype=torch.int32).pin_memory(),
                  torch.empty((max(1, n // 2), 2), dtype=torch.uint8).pin_memory()]
-        ka.reset()
-        ka.submit(rs)
-        with pytest.raises(pkg.KmerError) as e:
-            pkg.kmer_analysis_query_into(ka.handle, *[t.data_ptr() for t in small], max(1, n // 2), pkg.KMER_HOST)
-        assert e.value.code == pkg.KMER_ERR_INVALID_ARG
+        for where in (pkg.KMER_HOST, pkg.KMER_HOST_STAGED):
+            ka.reset()
+            ka.submit(rs)
+            with pytest.raises(pkg.KmerError) as e:
+                pkg.kmer_analysis_query_into(ka.handle, *[t.data_ptr() for t in small], max(1, n // 2), where)
+            assert e.value.code == pkg.KMER_ERR_INVALID_ARG
         pageable = [np.empty((n, W), np.uint64), np.empty(n, np.uint32), np.empty((n, 8), np.uint32),
                     np.empty((n, 2), np.uint8)]
         ka.reset()

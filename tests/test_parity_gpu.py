@@ -91,6 +91,26 @@ def test_metagenome_slice_k31(torch_cuda):
     assert st["l2_bits"] > 0
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_staged_host_reads(torch_cuda, pinned):
+    """Reads moved to the device by the copy engines (KMER_HOST_STAGED) from
+    page-locked or pageable host memory, packed into a reused readset: the
+    oracle's results."""
+    rs = synth.generate(synth.METAGENOME_2G.scaled(20_000, seed=21))
+    b, q, o = (torch_cuda.from_numpy(a) for a in (rs.bases, rs.quals, rs.offsets.view(np.int64)))
+    if pinned:
+        b, q, o = b.pin_memory(), q.pin_memory(), o.pin_memory()
+    r = pkg.ReadSet(b[:1000].clone(), q[:1000].clone(), torch_cuda.tensor([0, 1000], dtype=torch_cuda.int64),
+                    staged=True)
+    r.pack(b, q, o, staged=True)
+    ka = pkg.KmerAnalysis(31)
+    ka.submit(r)
+    got = ka.results()
+    ka.close()
+    r.close()
+    assert_same(got, oracle.run(rs.bases, rs.quals, rs.offsets, oracle.Params(k=31)), "staged reads")
+
+
 @pytest.mark.parametrize("variant", [pkg.KMER_VARIANT_PARTITIONED, pkg.KMER_VARIANT_HBM_TABLE])
 @pytest.mark.parametrize("k", [1, 3, 15, 31, 33, 61, 63, 65, 95, 97, 127])
 def test_every_word_boundary(torch_cuda, k, variant):
@@ -158,6 +178,33 @@ def test_heavy_hitter_exact_counts(torch_cuda):
     assert len(res) == 1 and int(res.count[0]) == n * (L - 20)
     assert list(res.ext[0]) == [n * (L - 21), 0, 0, 0, n * (L - 21), 0, 0, 0]
     ka.close(); r.close()
+
+
+def test_deep_coverage_tallies(torch_cuda):
+    """A 3 kbp genome at about 300x: counts and per-side tallies in the
+    hundreds (a tally far above any that low-coverage tests reach)."""
+    rs = synth.generate(synth.SINGLE_GENOME.scaled(6_000, genome_len_min=3_000, genome_len_max=3_000, seed=11))
+    got, _ = check(rs, 31, "deep coverage", torch=torch_cuda)
+    assert int(got.count.max()) > 200 and int(got.ext.max()) > 128
+
+
+def test_homopolymer_in_shared_table_leaf(torch_cuda):
+    """One k-mer seen 13 000 times among 20 000 others (its leaf has fewer
+    than 65 536 records): its left-A and right-A tallies are exact."""
+    L, n = 150, 100
+    hp = [(b"A" * L, b"I" * L)] * n
+    other = synth.generate(synth.SINGLE_GENOME.scaled(200, seed=12))
+    bases = np.concatenate([np.frombuffer(b"".join(r[0] for r in hp), np.uint8), other.bases])
+    quals = np.concatenate([np.frombuffer(b"".join(r[1] for r in hp), np.uint8), other.quals])
+    offsets = np.concatenate([np.arange(n, dtype=np.uint64) * L, other.offsets.astype(np.uint64) + n * L])
+    got, _ = check(_Reads(bases, quals, offsets), 21, "homopolymer", torch=torch_cuda)
+    a = got.count.argmax()
+    assert int(got.count[a]) == n * (L - 20)
+
+
+class _Reads:
+    def __init__(self, bases, quals, offsets):
+        self.bases, self.quals, self.offsets = bases, quals, offsets
 
 
 def test_fallback_when_leaves_do_not_fit(torch_cuda):
