@@ -661,7 +661,7 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
         if (!sjobs.empty()) {
             CK(launch_scatter(W, h->d_sjobs.as<Job>(), h->d_tile_off.as<unsigned long long>(), (unsigned)sjobs.size(),
-                              tile_off.back(), g.p1, h->stream));
+                              tile_off.back(), g.p1, g.k, h->stream));
             h->st.launches++;
         }
         TRY(prof_end(h, kmer_analysis::STG_SCATTER));

@@ -58,7 +58,7 @@ struct BJob {
 struct Wave {
     std::vector<unsigned> ids;  // job indices, grouped by key width
     struct Cls {
-        unsigned W, first, count, max_p1, max_p2, cap_max;
+        unsigned W, first, count, max_p1, max_p2, cap_max, min_k;
         unsigned long long tiles, leaves;
     };
     std::vector<Cls> classes;
@@ -240,7 +240,8 @@ int capture_wave(kmer_batch* b, Wave& w) {
         if (e == cudaSuccess) e = cudaMemsetAsync(b->misc.as<Misc>() + id, 0, sizeof(Misc), b->stream);
     for (size_t ci = 0; ci < w.classes.size() && e == cudaSuccess; ++ci) {
         const auto& c = w.classes[ci];
-        e = launch_scatter(c.W, dj + c.first, maps + w.tile_off_at[ci], c.count, c.tiles, c.max_p1, b->stream);
+        e = launch_scatter(c.W, dj + c.first, maps + w.tile_off_at[ci], c.count, c.tiles, c.max_p1, c.min_k,
+                           b->stream);
     }
     for (size_t ci = 0; ci < w.classes.size() && e == cudaSuccess; ++ci) {
         const auto& c = w.classes[ci];
@@ -359,11 +360,12 @@ int build_plan(kmer_batch* b) {
             so += j.scratch_bytes;
             zo += zero_bytes_of(j);
             if (w.classes.empty() || w.classes.back().W != j.W)
-                w.classes.push_back({j.W, s, 0, 0, 0, j.cap_max, 0, 0});
+                w.classes.push_back({j.W, s, 0, 0, 0, j.cap_max, KMER_MAX_K, 0, 0});
             auto& c = w.classes.back();
             c.count++;
             c.max_p1 = std::max(c.max_p1, j.g.p1);
             c.max_p2 = std::max(c.max_p2, j.g.p2);
+            c.min_k = std::min(c.min_k, j.g.k);
         }
         TRY(capture_wave(b, w));
     }

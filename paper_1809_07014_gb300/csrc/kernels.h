@@ -38,10 +38,12 @@ cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsig
                                unsigned long long cap, int num_sms, cudaStream_t s);
 
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
-// tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles.
+// tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles; min_k =
+// the smallest k of the jobs (one-word keys with k >= 17 roll on their high
+// half).
 size_t scatter_smem_bytes(unsigned W, unsigned p1);
 cudaError_t launch_scatter(unsigned W, const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
-                           unsigned long long tiles, unsigned max_p1, cudaStream_t s);
+                           unsigned long long tiles, unsigned max_p1, unsigned min_k, cudaStream_t s);
 
 // Per analysis: level-2 tile counts, leaf capacities and leaf region bases;
 // then job_tile_off = prefix of the analyses' level-2 tiles (device array).

@@ -10,7 +10,10 @@
 
 namespace kmer {
 
-template <int W>
+// HI (one word, k >= 17): the window's first base sits in the high 32 bits
+// of the word, so the base leaving the window and the complement entering the
+// reverse strand touch that half only.
+template <int W, bool HI = false>
 struct Roll {
     unsigned long long fwd[W], rc[W];
     unsigned long long gh0, gh1;  // good bits of the last 128 bases, bit m = base t-1-m
@@ -64,10 +67,11 @@ struct Roll {
         bool emit = false;
         if (t >= k && last_n < (long long)(t - k)) {
             emit = true;
-            const unsigned long long i = t - k;
+            // the history holds zeros before the read's first base, so the
+            // first window finds no left extension, and `good` is 0 past the end
             const unsigned lgood = k < 64 ? (unsigned)(gh0 >> k) & 1u : (unsigned)(gh1 >> (k - 64)) & 1u;
-            unsigned lc = (i >= 1 && lgood) ? out + 1 : 0;
-            unsigned rcd = (t < L && good) ? b + 1 : 0;
+            unsigned lc = lgood ? out + 1 : 0;
+            unsigned rcd = good ? b + 1 : 0;
             // canonical: the lexicographically smaller of forward and reverse complement
             bool flip = false;
 #pragma unroll
@@ -103,11 +107,11 @@ struct Roll {
 
 // k <= 31: the whole k-mer fits one word; positions and the quality history
 // fit 32 bits (reads are shorter than 2^31 bases).
-template <>
-struct Roll<1> {
+template <bool HI>
+struct Roll<1, HI> {
     unsigned long long fwd, rc, mask, cur;
     unsigned curn, curg, gh, out, L, k, sh;
-    int last_n;
+    int first_ok;  // first step whose window holds no N: last N position + k + 1
     uint4 nxt;
     const PackedBlock* blk;
 
@@ -120,7 +124,7 @@ struct Roll<1> {
         mask = low_mask(2 * k);
         fwd = rc = cur = 0;
         curn = curg = gh = out = 0;
-        last_n = -1;
+        first_ok = (int)k;
         nxt = L ? __ldg(reinterpret_cast<const uint4*>(blk)) : make_uint4(0, 0, 0, 0);
     }
 
@@ -144,10 +148,11 @@ struct Roll<1> {
             curg >>= 1;
         }
         bool emit = false;
-        if (t >= k && last_n < (int)(t - k)) {
+        if ((int)t >= first_ok) {
             emit = true;
-            unsigned lc = (t > k && ((gh >> k) & 1u)) ? out + 1 : 0;
-            unsigned rcd = (in && good) ? b + 1 : 0;
+            // gh is zero before the first base and `good` is 0 past the end
+            unsigned lc = ((gh >> k) & 1u) ? out + 1 : 0;
+            unsigned rcd = good ? b + 1 : 0;
             const bool flip = rc < fwd;
             key[0] = flip ? rc : fwd;
             if (flip) {  // the key reads the other strand: swap sides, complement bases
@@ -159,11 +164,16 @@ struct Roll<1> {
             rcode = rcd;
         }
         if (in) {
-            out = (unsigned)(fwd >> sh) & 3u;
+            if (HI) {
+                out = ((unsigned)(fwd >> 32) >> (sh - 32)) & 3u;
+                rc = (rc >> 2) | ((unsigned long long)((3u - b) << (sh - 32)) << 32);
+            } else {
+                out = (unsigned)(fwd >> sh) & 3u;
+                rc = (rc >> 2) | ((unsigned long long)(3u - b) << sh);
+            }
             fwd = ((fwd << 2) | b) & mask;
-            rc = (rc >> 2) | ((unsigned long long)(3u - b) << sh);
             gh = (gh << 1) | good;
-            if (isn) last_n = (int)t;
+            if (isn) first_ok = (int)(t + k + 1);
         }
         return emit;
     }
