@@ -437,7 +437,7 @@ def run_ours(args):
     line["clocks"] = clocks.stop()
     line["gpu_launches"] = launches
     line["stats"] = {k: st[k] for k in ("windows", "distinct", "survivors", "passes", "l1_bits", "l2_bits",
-                                        "retries", "fallback_leaves", "leaf_table_slots", "device_bytes")}
+                                        "retries", "fallback_leaves", "leaf_splits", "leaf_table_slots", "device_bytes")}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -113,8 +113,11 @@ Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long lon
     g.W = (2 * k + 63) / 64;
     g.hb = 2 * k - 64 * (g.W - 1);
     g.bt = g.W == 1 ? 2 * k : 64;
-    // about half a leaf table of distinct keys per leaf
-    const unsigned long long target = std::max(64u, cap_max / 2);
+    // up to 0.7 of a leaf table of (estimated) distinct keys per leaf: the
+    // estimate carries a 15 % margin, so leaves hold about 0.3-0.6 of a table
+    // (fewer, fuller leaves amortise each leaf's sweep and barriers; a leaf
+    // that overflows is counted again in key ranges)
+    const unsigned long long target = std::max(64ull, (unsigned long long)cap_max * 7 / 10);
     unsigned p = leaf_bits ? leaf_bits : ceil_log2((basis + target - 1) / target);
     const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
     p = std::max(p, need);

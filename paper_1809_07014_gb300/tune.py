@@ -74,13 +74,13 @@ def _run(rs: ReadSet, k: int, reps: int, stream, **params) -> tuple[float, dict]
     return best, st
 
 
-def autotune(rs: ReadSet, k: int, reps: int = 2, stream=None, keys_per_leaf=(0.2, 0.3, 0.4, 0.5),
+def autotune(rs: ReadSet, k: int, reps: int = 2, stream=None, keys_per_leaf=(0.3, 0.4, 0.5, 0.6),
              l1_shifts=(-1, 0)) -> Tuning:
     """Time candidate geometries for k on readset `rs`; return the fastest."""
     ms_default, st = _run(rs, k, reps, stream)
     windows, distinct, surv = st["windows"], st["distinct"], st["survivors"]
     slots = st["leaf_table_slots"]
-    best = (ms_default, 0.5, 0)
+    best = (ms_default, 0.6, 0)
     if windows:
         for frac in keys_per_leaf:
             per_leaf = frac * slots
@@ -97,7 +97,7 @@ def autotune(rs: ReadSet, k: int, reps: int = 2, stream=None, keys_per_leaf=(0.2
                     best = (ms, per_leaf, shift)
     W = (2 * k + 63) // 64
     return Tuning(k=k, words=W, windows=windows, distinct_ratio=distinct / max(1, windows),
-                  survivor_ratio=surv / max(1, windows), keys_per_leaf=best[1] if best[1] > 1 else 0.5 * slots,
+                  survivor_ratio=surv / max(1, windows), keys_per_leaf=best[1] if best[1] > 1 else 0.6 * slots,
                   l1_shift=best[2], ms_best=best[0], ms_default=ms_default)
 
 
