@@ -113,21 +113,45 @@ struct RepartTile {
     const unsigned long long* src;
 };
 
+// A CTA's tiles come in increasing order, gridDim.x apart, and a bucket spans
+// many tiles: the bucket of the next tile is the previous one or the one
+// after it, found with one or two loads; a search (a chain of dependent
+// loads, each an L2 round trip) is needed only on a CTA's first tile of an
+// analysis or after a jump over several buckets.
+struct TileCursor {
+    unsigned ji = 0xFFFFFFFFu, bucket = 0;
+};
+
 __device__ __forceinline__ RepartTile repart_tile_at(const Job* __restrict__ jobs,
                                                      const unsigned long long* __restrict__ job_tile_off,
                                                      const unsigned n_jobs, const unsigned long long gt,
-                                                     const unsigned S) {
+                                                     const unsigned S, TileCursor& cur) {
     RepartTile rt;
-    rt.ji = job_of(job_tile_off, n_jobs, gt);
+    if (cur.ji == 0xFFFFFFFFu || (cur.ji + 1 < n_jobs && job_tile_off[cur.ji + 1] <= gt)) {
+        cur.ji = job_of(job_tile_off, n_jobs, gt);
+        cur.bucket = 0xFFFFFFFFu;
+    }
+    rt.ji = cur.ji;
     const Job& j = jobs[rt.ji];
     const unsigned long long tile = gt - job_tile_off[rt.ji];
+    const unsigned last = (1u << j.g.p1) - 1;
     // bucket of this tile: last b with tile_prefix[b] <= tile
-    unsigned lo = 0, hi = (1u << j.g.p1) - 1;
-    while (lo < hi) {
-        const unsigned mid = (lo + hi + 1) >> 1;
-        if (j.tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+    unsigned b = cur.bucket;
+    if (b != 0xFFFFFFFFu && b < last && j.tile_prefix[b + 1] <= tile) {
+        ++b;
+        if (b < last && j.tile_prefix[b + 1] <= tile) b = 0xFFFFFFFFu;  // more than one bucket ahead
     }
-    rt.bucket = lo;
+    if (b == 0xFFFFFFFFu) {
+        unsigned lo = cur.bucket == 0xFFFFFFFFu ? 0 : cur.bucket, hi = last;
+        while (lo < hi) {
+            const unsigned mid = (lo + hi + 1) >> 1;
+            if (j.tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        b = lo;
+    }
+    cur.bucket = b;
+    rt.bucket = b;
+    const unsigned lo = b;
     const unsigned long long f = j.l1_fill[lo], c = j.l1_cap[lo];
     const unsigned long long n = f < c ? f : c;
     const unsigned long long begin = (tile - j.tile_prefix[lo]) * S;
@@ -153,6 +177,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
     unsigned long long gt = blockIdx.x;
     unsigned long long rec[U][W];
     RepartTile rt{};
+    TileCursor cur;
     auto load = [&](const RepartTile& x) {
 #pragma unroll
         for (unsigned u = 0; u < U; ++u) {
@@ -162,7 +187,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
         }
     };
     if (gt < all) {
-        rt = repart_tile_at(jobs, job_tile_off, n_jobs, gt, S);
+        rt = repart_tile_at(jobs, job_tile_off, n_jobs, gt, S, cur);
         load(rt);
     }
     __syncthreads();
@@ -189,7 +214,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
         const unsigned long long ngt = gt + gridDim.x;
         RepartTile nrt{};
         if (ngt < all) {
-            nrt = repart_tile_at(jobs, job_tile_off, n_jobs, ngt, S);
+            nrt = repart_tile_at(jobs, job_tile_off, n_jobs, ngt, S, cur);
             load(nrt);
         }
         L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[rt.bucket], j.l2_leafcap[rt.bucket], rt.bucket << j.g.p2};
