@@ -602,6 +602,9 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         for (unsigned b = 0; b < P1; ++b) starts[b + 1] = starts[b] + caps[b];
         const unsigned long long l1_total = starts[P1];
         TRY(h->l1_rec.ensure(l1_total * 8 * W + 64));
+        // the repartition's bulk copies start on 16-byte boundaries of this region
+        if (reinterpret_cast<uintptr_t>(h->l1_rec.p) & 15)
+            return fail(KMER_ERR_CUDA, "level-1 record buffer is not 16-byte aligned");
         TRY(h->l1_start.ensure((P1 + 1) * 8));
         TRY(h->l1_cap.ensure(P1 * 8));
         TRY(h->l1_fill.ensure(P1 * 8));

@@ -144,6 +144,8 @@ int bind_job(kmer_batch* b, BJob& j, unsigned char* scratch, unsigned char* zero
     d.pass = 0;
     size_t o = 0;
     d.l1_rec = reinterpret_cast<unsigned long long*>(scratch + o);
+    // the repartition's bulk copies start on 16-byte boundaries of this region
+    if (reinterpret_cast<uintptr_t>(d.l1_rec) & 15) return fail(KMER_ERR_CUDA, "level-1 records not 16-byte aligned");
     o += align_up(j.l1_total * 8 * j.W + 64);
     // bucket starts and capacities never change: kept in the job's own buffer
     TRY(j.consts.ensure((2 * P1 + 1) * 8));

@@ -224,8 +224,160 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
     }
 }
 
+// ------------------------------------------------------------------------
+// One-word records: tiles arrive by bulk asynchronous copies (the TMA engine,
+// cp.async.bulk completing on an mbarrier) into two shared-memory buffers, two
+// tiles ahead of the one being flushed, so no registers hold records in
+// flight and the flush reads each record straight from the tile buffer.
+constexpr unsigned kTmaWaitLimit = 1u << 20;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `phase` of an mbarrier to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
+    for (unsigned i = 0; i < kTmaWaitLimit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// One thread: announce `bytes` on the barrier and start the bulk copy
+// (both addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Records of a tile sit `lead` records into its buffer: the copy starts at
+// the 16-byte boundary at or below the tile's first record (the level-1
+// region is 256-byte aligned and padded at its end, so the rounded range
+// stays inside it).
+__device__ __forceinline__ unsigned tile_lead(const RepartTile& rt) {
+    return (unsigned)(reinterpret_cast<unsigned long long>(rt.src) & 15ull) >> 3;
+}
+
+__device__ __forceinline__ void issue_tile(const RepartTile& rt, unsigned long long* buf, unsigned long long* bar) {
+    const unsigned lead = tile_lead(rt);
+    const unsigned bytes = ((lead + rt.cnt) * 8u + 15u) & ~15u;
+    bulk_load(buf, rt.src - lead, bytes, bar);
+}
+
+constexpr unsigned kTmaTile = RepartShape<1>::S;
+
+__host__ __device__ inline size_t repart_tma_smem_bytes(unsigned pmax) {
+    return 2 * ((size_t)kTmaTile + 2) * 8 + 16 + (size_t)pmax * 8 + 3 * (size_t)pmax * 4 + (size_t)kTmaTile * 4 + 128;
+}
+
+// A tile buffer's state: the tile it holds or is receiving, whether a copy
+// into it is still unwaited, and the barrier phase that copy completes.
+struct TmaSlot {
+    RepartTile rt;
+    bool pending;
+    unsigned phase;
+};
+
+template <unsigned MAXPER>
+__global__ void __launch_bounds__(kRepartThreads, 2) repart_tma_kernel(const Job* __restrict__ jobs,
+                                                                     const unsigned long long* __restrict__ job_tile_off,
+                                                                     const unsigned n_jobs, const unsigned pmax) {
+    constexpr unsigned S = kTmaTile, U = S / kRepartThreads;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* const buf0 = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* const buf1 = buf0 + S + 2;
+    unsigned long long* const bar = buf1 + S + 2;  // two mbarriers
+    StageBufs sb;
+    sb.stage = nullptr;
+    sb.meta = nullptr;
+    sb.wbase = bar + 2;
+    sb.ok_end = reinterpret_cast<unsigned*>(sb.wbase + pmax);
+    sb.hist = sb.ok_end + pmax;
+    sb.lbase = sb.hist + pmax;
+    sb.order = sb.lbase + pmax;
+    sb.warp_tmp = sb.order + S;
+    for (unsigned d = threadIdx.x; d < pmax; d += kRepartThreads) sb.hist[d] = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    const unsigned long long all = job_tile_off[n_jobs];
+    TileCursor cur;
+    TmaSlot s0{{}, false, 0}, s1{{}, false, 0};
+    auto start = [&](TmaSlot& sl, unsigned long long* bf, unsigned long long* br, unsigned long long g) {
+        sl.rt = repart_tile_at(jobs, job_tile_off, n_jobs, g, S, cur);
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tile(sl.rt, bf, br);
+        }
+        sl.pending = true;
+    };
+    // waits for the slot's tile, flushes it, and refills the slot with the
+    // tile two steps ahead; false after a wait that gave up
+    auto run = [&](TmaSlot& sl, unsigned long long* bf, unsigned long long* br, unsigned long long gt) -> bool {
+        const RepartTile t = sl.rt;
+        const Job& j = jobs[t.ji];
+        if (!mbar_wait(br, sl.phase)) {
+            if (threadIdx.x == 0) set_status(j, ST_TIMEOUT);
+            return false;
+        }
+        sl.pending = false;
+        sl.phase ^= 1u;
+        const unsigned long long* tile = bf + tile_lead(t);
+        const unsigned P2 = 1u << j.g.p2;
+        const unsigned shift = j.g.zl_bits() - j.g.p2;
+        unsigned m[U];
+#pragma unroll
+        for (unsigned u = 0; u < U; ++u) {
+            const unsigned e = u * kRepartThreads + threadIdx.x;
+            m[u] = 0xFFFFFFFFu;
+            if (e < t.cnt) {
+                const unsigned sub = (unsigned)((tile[e] >> 6) >> shift) & (P2 - 1u);
+                m[u] = (sub << 16) | atomicAdd(&sb.hist[sub], 1u);
+            }
+        }
+        StageBufs b = sb;
+        b.stage = const_cast<unsigned long long*>(tile);
+        L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[t.bucket], j.l2_leafcap[t.bucket], t.bucket << j.g.p2};
+        flush_stage_regs<1, MAXPER, L2Dest, kRepartThreads, U>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW, m);
+        // the flush ends on a barrier: every thread is done with this buffer
+        const unsigned long long g2 = gt + 2ull * gridDim.x;
+        if (g2 < all) start(sl, bf, br, g2);
+        return true;
+    };
+    if (blockIdx.x < all) start(s0, buf0, &bar[0], blockIdx.x);
+    if (blockIdx.x + (unsigned long long)gridDim.x < all) start(s1, buf1, &bar[1], blockIdx.x + gridDim.x);
+    for (unsigned long long gt = blockIdx.x; gt < all; gt += 2ull * gridDim.x) {
+        if (!run(s0, buf0, &bar[0], gt)) break;
+        if (gt + gridDim.x >= all) break;
+        if (!run(s1, buf1, &bar[1], gt + gridDim.x)) break;
+    }
+    // after a wait that gave up: no copy may still be writing this CTA's shared memory
+    if (s0.pending) mbar_wait(&bar[0], s0.phase);
+    if (s1.pending) mbar_wait(&bar[1], s1.phase);
+}
+
 size_t repart_smem_bytes(unsigned W, unsigned p2) {
-    return stage_smem_bytes(W, repart_tile(W), 1u << p2);
+    return W == 1 ? repart_tma_smem_bytes(1u << p2) : stage_smem_bytes(W, repart_tile(W), 1u << p2);
 }
 
 cudaError_t launch_l2_plan(const Job* jobs, unsigned n_jobs, unsigned long long* job_tile_off, cudaStream_t s) {
@@ -246,12 +398,29 @@ static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* j
     return cudaGetLastError();
 }
 
+template <unsigned MAXPER>
+static cudaError_t launch_repart_tma(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
+                                     unsigned max_p2, int num_sms, cudaStream_t s) {
+    const size_t smem = repart_tma_smem_bytes(1u << max_p2);
+    cudaError_t e =
+        cudaFuncSetAttribute(repart_tma_kernel<MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    repart_tma_kernel<MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
+    return cudaGetLastError();
+}
+
 template <int W>
 static cudaError_t launch_repart_w(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
                                    unsigned max_p2, int num_sms, cudaStream_t s) {
-    if ((1u << max_p2) <= 2 * kRepartThreads)
-        return launch_repart_wp<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
-    return launch_repart_wp<W, kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+    if constexpr (W == 1) {
+        if ((1u << max_p2) <= 2 * kRepartThreads)
+            return launch_repart_tma<2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        return launch_repart_tma<kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+    } else {
+        if ((1u << max_p2) <= 2 * kRepartThreads)
+            return launch_repart_wp<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        return launch_repart_wp<W, kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+    }
 }
 
 cudaError_t launch_repart(unsigned W, const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
