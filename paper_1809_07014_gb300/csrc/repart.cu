@@ -11,7 +11,7 @@ constexpr unsigned kRepartThreads = 512;
 
 template <int W>
 struct RepartShape {
-    static constexpr unsigned S = W == 1 ? 4096 : (W == 2 ? 3072 : 2048);  // records per tile
+    static constexpr unsigned S = W == 1 ? 4096 : 2048;  // records per tile
 };
 
 __host__ __device__ inline unsigned repart_tile(unsigned W) {
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __
 }
 
 // ------------------------------------------------------------------------
-// One-word records: tiles arrive by bulk asynchronous copies (the TMA engine,
+// One- and two-word records: tiles arrive by bulk asynchronous copies (the TMA engine,
 // cp.async.bulk completing on an mbarrier) into two shared-memory buffers, two
 // tiles ahead of the one being flushed, so no registers hold records in
 // flight and the flush reads each record straight from the tile buffer.
@@ -274,16 +274,18 @@ __device__ __forceinline__ unsigned tile_lead(const RepartTile& rt) {
     return (unsigned)(reinterpret_cast<unsigned long long>(rt.src) & 15ull) >> 3;
 }
 
+template <int W>
 __device__ __forceinline__ void issue_tile(const RepartTile& rt, unsigned long long* buf, unsigned long long* bar) {
     const unsigned lead = tile_lead(rt);
-    const unsigned bytes = ((lead + rt.cnt) * 8u + 15u) & ~15u;
+    const unsigned bytes = ((lead + rt.cnt * W) * 8u + 15u) & ~15u;
     bulk_load(buf, rt.src - lead, bytes, bar);
 }
 
-constexpr unsigned kTmaTile = RepartShape<1>::S;
-
-__host__ __device__ inline size_t repart_tma_smem_bytes(unsigned pmax) {
-    return 2 * ((size_t)kTmaTile + 2) * 8 + 16 + (size_t)pmax * 8 + 3 * (size_t)pmax * 4 + (size_t)kTmaTile * 4 + 128;
+// Shared memory: two tile buffers (each a tile plus 16 bytes of lead), two
+// mbarriers, then the staging arrays without a meta array.
+__host__ __device__ inline size_t repart_tma_smem_bytes(unsigned W, unsigned pmax) {
+    const size_t S = W == 1 ? RepartShape<1>::S : RepartShape<2>::S;
+    return 2 * (S * W + 2) * 8 + 16 + (size_t)pmax * 8 + 3 * (size_t)pmax * 4 + S * 4 + 128;
 }
 
 // A tile buffer's state: the tile it holds or is receiving, whether a copy
@@ -294,15 +296,16 @@ struct TmaSlot {
     unsigned phase;
 };
 
-template <unsigned MAXPER>
+template <int W, unsigned MAXPER>
 __global__ void __launch_bounds__(kRepartThreads, 2) repart_tma_kernel(const Job* __restrict__ jobs,
                                                                      const unsigned long long* __restrict__ job_tile_off,
                                                                      const unsigned n_jobs, const unsigned pmax) {
-    constexpr unsigned S = kTmaTile, U = S / kRepartThreads;
+    static_assert(W <= 2, "tile buffers sized for one- and two-word records");
+    constexpr unsigned S = RepartShape<W>::S, U = S / kRepartThreads;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* const buf0 = reinterpret_cast<unsigned long long*>(smem);
-    unsigned long long* const buf1 = buf0 + S + 2;
-    unsigned long long* const bar = buf1 + S + 2;  // two mbarriers
+    unsigned long long* const buf1 = buf0 + S * W + 2;
+    unsigned long long* const bar = buf1 + S * W + 2;  // two mbarriers
     StageBufs sb;
     sb.stage = nullptr;
     sb.meta = nullptr;
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_tma_kernel(const Job
         sl.rt = repart_tile_at(jobs, job_tile_off, n_jobs, g, S, cur);
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tile(sl.rt, bf, br);
+            issue_tile<W>(sl.rt, bf, br);
         }
         sl.pending = true;
     };
@@ -351,14 +354,14 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_tma_kernel(const Job
             const unsigned e = u * kRepartThreads + threadIdx.x;
             m[u] = 0xFFFFFFFFu;
             if (e < t.cnt) {
-                const unsigned sub = (unsigned)((tile[e] >> 6) >> shift) & (P2 - 1u);
+                const unsigned sub = (unsigned)((tile[(size_t)e * W + W - 1] >> 6) >> shift) & (P2 - 1u);
                 m[u] = (sub << 16) | atomicAdd(&sb.hist[sub], 1u);
             }
         }
         StageBufs b = sb;
         b.stage = const_cast<unsigned long long*>(tile);
         L2Dest dest{j.l2_fill, j.l2_leaf_start, j.l2_base[t.bucket], j.l2_leafcap[t.bucket], t.bucket << j.g.p2};
-        flush_stage_regs<1, MAXPER, L2Dest, kRepartThreads, U>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW, m);
+        flush_stage_regs<W, MAXPER, L2Dest, kRepartThreads, U>(b, S, P2, dest, j.l2_rec, j.status, ST_L2_OVERFLOW, m);
         // the flush ends on a barrier: every thread is done with this buffer
         const unsigned long long g2 = gt + 2ull * gridDim.x;
         if (g2 < all) start(sl, bf, br, g2);
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kRepartThreads, 2) repart_tma_kernel(const Job
 }
 
 size_t repart_smem_bytes(unsigned W, unsigned p2) {
-    return W == 1 ? repart_tma_smem_bytes(1u << p2) : stage_smem_bytes(W, repart_tile(W), 1u << p2);
+    return W <= 2 ? repart_tma_smem_bytes(W, 1u << p2) : stage_smem_bytes(W, repart_tile(W), 1u << p2);
 }
 
 cudaError_t launch_l2_plan(const Job* jobs, unsigned n_jobs, unsigned long long* job_tile_off, cudaStream_t s) {
@@ -398,24 +401,24 @@ static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* j
     return cudaGetLastError();
 }
 
-template <unsigned MAXPER>
+template <int W, unsigned MAXPER>
 static cudaError_t launch_repart_tma(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
                                      unsigned max_p2, int num_sms, cudaStream_t s) {
-    const size_t smem = repart_tma_smem_bytes(1u << max_p2);
+    const size_t smem = repart_tma_smem_bytes(W, 1u << max_p2);
     cudaError_t e =
-        cudaFuncSetAttribute(repart_tma_kernel<MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(repart_tma_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    repart_tma_kernel<MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
+    repart_tma_kernel<W, MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
     return cudaGetLastError();
 }
 
 template <int W>
 static cudaError_t launch_repart_w(const Job* jobs, const unsigned long long* job_tile_off, unsigned n_jobs,
                                    unsigned max_p2, int num_sms, cudaStream_t s) {
-    if constexpr (W == 1) {
+    if constexpr (W <= 2) {
         if ((1u << max_p2) <= 2 * kRepartThreads)
-            return launch_repart_tma<2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
-        return launch_repart_tma<kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+            return launch_repart_tma<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
+        return launch_repart_tma<W, kMaxStageDest / kRepartThreads>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
     } else {
         if ((1u << max_p2) <= 2 * kRepartThreads)
             return launch_repart_wp<W, 2>(jobs, job_tile_off, n_jobs, max_p2, num_sms, s);
