@@ -58,10 +58,14 @@ def parse_args():
     ap.add_argument("--large", action="store_true",
                     help="serve: also run the 15-Gbase, 500-genome instance at k=55 within a 180 GB budget")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-threads", type=int, default=2, help="host threads of the end-to-end pipeline")
-    ap.add_argument("--e2e-io", choices=["staged", "in-place"], default="in-place",
+    ap.add_argument("--e2e-threads", type=int, default=3, help="host threads of the end-to-end pipeline")
+    ap.add_argument("--e2e-steps", type=int, default=24,
+                    help="end-to-end steps of the several-thread run (at least --steps): the pipeline "
+                         "fills and drains once per run")
+    ap.add_argument("--e2e-io", choices=["staged", "in-place"], default="staged",
                     help="end to end with several threads: host buffers moved by the copy engines "
-                         "(KMER_HOST_STAGED) or read and written in place by the kernels (KMER_HOST)")
+                         "(KMER_HOST_STAGED, the counting of one step at a time) or read and written in "
+                         "place by the kernels (KMER_HOST)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -355,11 +359,15 @@ def run_ours(args):
             "config": config_of(args, recipe, n_bases), "roofline": roofline}
 
     # ---- end to end through the C ABI from pinned host buffers: every step packs
-    # its reads from pinned host memory and writes its survivors into pinned
-    # host memory (in place by the kernels, or moved by the copy engines with
-    # --e2e-io staged).  Several host threads, each with its own readset,
-    # analysis and stream, take turns; the single-thread figure (in place) is
-    # reported beside.
+    # its reads from pinned host memory and copies its survivors into pinned
+    # host memory.  Several host threads, each with its own readset, analysis
+    # and stream, take turns.  Staged (the default): the reads and results
+    # cross the host link by the copy engines (kmer_readset_pack with
+    # KMER_HOST_STAGED, kmer_analysis_copy_results), and the counting itself
+    # (kmer_analysis_query) runs one step at a time under a host lock, so one
+    # step's kernels have the SMs while other steps' transfers run.  In place:
+    # the kernels read and write the pinned buffers (KMER_HOST).  The
+    # single-thread figure (in place) is reported beside.
     if not args.no_e2e:
         import threading
         ka.close()  # its device buffers go back to the pool for the two lanes below
@@ -382,14 +390,23 @@ def run_ours(args):
                 "ka": pkg.KmerAnalysis(args.k, stream=st_l, variant=variant, leaf_bits=args.leaf_bits),
                 "windows": 0, "d2h": 0})
 
+        count_lock = threading.Lock()
+
         def e2e_step(ln, stg):
             # reads from pinned host buffers; survivors into pinned host buffers
             ln["rs"].pack(b_h, q_h, o_h, stream=ln["stream"], staged=stg)
-            ln["ka"].reset()
-            ln["ka"].submit(ln["rs"])
-            vv = pkg.kmer_analysis_query_into(ln["ka"].handle, ln["keys"].data_ptr(), ln["cnt"].data_ptr(),
-                                              ln["ext"].data_ptr(), ln["cls"].data_ptr(), cap,
-                                              pkg.KMER_HOST_STAGED if stg else pkg.KMER_HOST)
+            if stg:
+                with count_lock:
+                    ln["ka"].reset()
+                    ln["ka"].submit(ln["rs"])
+                    vv = pkg.kmer_analysis_query(ln["ka"].handle)
+                pkg.kmer_analysis_copy_results(ln["ka"].handle, ln["keys"].data_ptr(), ln["cnt"].data_ptr(),
+                                               ln["ext"].data_ptr(), ln["cls"].data_ptr(), cap)
+            else:
+                ln["ka"].reset()
+                ln["ka"].submit(ln["rs"])
+                vv = pkg.kmer_analysis_query_into(ln["ka"].handle, ln["keys"].data_ptr(), ln["cnt"].data_ptr(),
+                                                  ln["ext"].data_ptr(), ln["cls"].data_ptr(), cap, pkg.KMER_HOST)
             ln["windows"] += int(vv.windows)
             ln["d2h"] += int(vv.n) * (8 * W + 4 + 32 + 2)
 
@@ -411,11 +428,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt1, w1 = reduce_over_ranks(time.perf_counter() - t0, lanes[0]["windows"], dev)
         # several threads taking turns
+        e2e_steps = max(args.steps, args.e2e_steps)
         for ln in lanes:
             ln["windows"] = ln["d2h"] = 0
         barrier()
         t0 = time.perf_counter()
-        ths = [threading.Thread(target=run_lane, args=(lanes[i], (args.steps + n_thr - 1 - i) // n_thr, staged))
+        ths = [threading.Thread(target=run_lane, args=(lanes[i], (e2e_steps + n_thr - 1 - i) // n_thr, staged))
                for i in range(n_thr)]
         for th in ths:
             th.start()
@@ -426,9 +444,10 @@ def run_ours(args):
         dt2, w2 = reduce_over_ranks(time.perf_counter() - t0, wins, dev)
         h2d = 2 * n_bases + 8 * (n_reads + 1)
         line["e2e"] = {"value": w2 / dt2, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": sum(ln["d2h"] for ln in lanes) // args.steps,
-                       "ms_per_step": 1e3 * dt2 / args.steps, "host_threads": n_thr,
-                       "host_io": "KMER_HOST_STAGED (copy engines)" if staged else "KMER_HOST (in place)",
+                       "d2h_bytes_per_step": sum(ln["d2h"] for ln in lanes) // e2e_steps,
+                       "ms_per_step": 1e3 * dt2 / e2e_steps, "steps": e2e_steps, "host_threads": n_thr,
+                       "host_io": ("KMER_HOST_STAGED (copy engines), one step counting at a time" if staged
+                                   else "KMER_HOST (in place)"),
                        "one_thread": {"value": w1 / dt1, "ms_per_step": 1e3 * dt1 / args.steps,
                                       "host_io": "KMER_HOST (in place)"}}
         for ln in lanes:
