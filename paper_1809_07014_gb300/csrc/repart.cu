@@ -160,10 +160,11 @@ __device__ __forceinline__ RepartTile repart_tile_at(const Job* __restrict__ job
     return rt;
 }
 
-// Persistent CTAs over the level-2 tiles of every analysis.  A tile's records
-// are requested (into registers) before the previous tile is flushed, so the
-// loads overlap the flush.  Shared memory is laid out for `pmax` leaves per
-// bucket, the largest fan-out of the launch.
+// Persistent CTAs over the level-2 tiles of every analysis (records of three
+// or four words; narrower records take repart_tma_kernel below).  A tile's
+// records are requested (into registers) before the previous tile is
+// flushed, so the loads overlap the flush.  Shared memory is laid out for
+// `pmax` leaves per bucket, the largest fan-out of the launch.
 template <int W, unsigned MAXPER>
 __global__ void __launch_bounds__(kRepartThreads, 2) repart_kernel(const Job* __restrict__ jobs,
                                                                  const unsigned long long* __restrict__ job_tile_off,
