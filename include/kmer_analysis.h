@@ -75,7 +75,10 @@ extern "C" {
  * kernels then touch only HBM, and the SMs are not held while the transfer
  * runs.  KMER_HOST reads and writes page-locked memory in place, which
  * overlaps the transfer with the kernels that make it; other host memory is
- * staged in both modes. */
+ * staged in both modes.  For one stream alone the in-place form is faster;
+ * host threads that pipeline steps on their own streams do better staging
+ * every transfer and running one step's counting at a time, so that each
+ * step's transfers overlap another step's kernels. */
 enum kmer_where { KMER_HOST = 0, KMER_DEVICE = 1, KMER_HOST_STAGED = 2 };
 enum kmer_ext_mode { KMER_EXT_DEPTH_ADAPTIVE = 0, KMER_EXT_STATIC = 1 };
 enum kmer_class { KMER_CLS_A = 0, KMER_CLS_C = 1, KMER_CLS_G = 2, KMER_CLS_T = 3,
@@ -224,7 +227,8 @@ int kmer_analysis_query_into(kmer_analysis_t *h, uint64_t *keys, uint32_t *count
 
 /* Copies the survivors of the last query to host memory: keys (n * W words),
  * count (n), ext (n * 8), cls (n * 2); any pointer may be NULL to skip that
- * array; `capacity` is the number of k-mers the buffers hold.  Synchronous.
+ * array; `capacity` is the number of k-mers the buffers hold.  The copy
+ * engines move them in 64 MB pieces; the call waits for them (synchronous).
  * Errors: BAD_STATE (no successful query), INVALID_ARG (capacity < n). */
 int kmer_analysis_copy_results(kmer_analysis_t *h, uint64_t *keys, uint32_t *count, uint32_t *ext, uint8_t *cls,
                                uint64_t capacity);
