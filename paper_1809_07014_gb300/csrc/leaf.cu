@@ -10,13 +10,16 @@
 //
 // Table (shared memory, planes of `cap_max` entries, a leaf uses the first
 // `cap` slots): the tail word of each slot (0 = empty; record tail with the
-// extension bits replaced by a mark bit; bit 0 = being published, W > 1
-// only), W-1 head words, and nine 16-bit tallies packed in five 32-bit planes:
+// extension bits replaced by a mark bit; bit 0 = being published, W > 2
+// only), W-1 head words (two-word keys keep tail and head side by side, one
+// 16-byte pair per slot claimed by a 128-bit CAS, in probe groups of two
+// slots), and nine 16-bit tallies packed in five 32-bit planes:
 // left A, C, G, T, "no left extension" (so that count = sum of the five left
 // lanes and needs no counter of its own), right A, C, G, T.  Slots are probed
-// in groups of four (one 32-byte read compares four keys).  A leaf with
-// 65536 records or more (where a 16-bit tally could wrap), or whose keys do
-// not fit, is recounted exactly by the HBM-table fallback.
+// in groups of 32 bytes of keys (one read compares four tails, or two
+// two-word keys).  A leaf with 65536 records or more (where a 16-bit tally
+// could wrap) is recounted exactly by the HBM-table fallback; one whose keys
+// do not fit its table is counted again in key ranges (leaf_split_kernel).
 //
 // Every plane is zero between leaves: the sweep clears each slot after
 // reading it, so no separate clearing pass is needed.
@@ -35,7 +38,7 @@ constexpr unsigned kMaxSubBits = 4;       // a leaf is split into at most 16 key
 
 template <int W>
 struct LeafShape {
-    static constexpr int U = W <= 2 ? 4 : 2;  // records per thread per batch
+    static constexpr int U = W == 1 ? 4 : 2;  // records per thread per batch
     static constexpr int B = U * kLeafThreads;
 };
 
@@ -118,6 +121,79 @@ __device__ __forceinline__ void bump(const Table& t, unsigned slot, unsigned q) 
     atomicAdd(&t.lanes[(q >> 1) * t.stride + slot], 1u << (16 * (q & 1)));
 }
 
+// Key words of a slot.  One-word keys: the tail plane.  Two-word keys:
+// (tail, head) pairs, 16 bytes per slot over the first two planes, claimed
+// whole by one 128-bit CAS.  Wider keys: the tail plane and W-1 head planes,
+// published with a busy bit.
+template <int W>
+__device__ __forceinline__ unsigned long long& slot_tail(const Table& t, unsigned s) {
+    return t.tail[W == 2 ? 2 * s : s];
+}
+template <int W>
+__device__ __forceinline__ unsigned long long slot_head(const Table& t, unsigned w, unsigned s) {
+    return W == 2 ? t.tail[2 * s + 1] : t.heads[(size_t)w * t.stride + s];
+}
+template <int W>
+__device__ __forceinline__ void clear_key(const Table& t, unsigned s) {
+    if (W == 2) {
+        *reinterpret_cast<ulonglong2*>(t.tail + 2 * s) = make_ulonglong2(0ull, 0ull);
+    } else {
+        t.tail[s] = 0ull;  // head words of an empty slot are never read
+    }
+}
+// Probe groups of a table of `cap` slots: 32 bytes of keys each.
+template <int W>
+__device__ __forceinline__ unsigned groups_of(unsigned cap) { return W == 2 ? cap / 2 : cap / 4; }
+
+// 128-bit compare-and-swap on shared memory: {lo, hi} replaces {0, 0};
+// returns the previous contents.
+__device__ __forceinline__ void cas128_shared(unsigned long long* p, unsigned long long lo, unsigned long long hi,
+                                              unsigned long long& old_lo, unsigned long long& old_hi) {
+    asm volatile(
+        "{\n\t.reg .b128 cmp, val, old;\n\t"
+        "mov.b128 cmp, {%4, %4};\n\t"
+        "mov.b128 val, {%2, %3};\n\t"
+        "atom.shared.cas.b128 old, [%5], cmp, val;\n\t"
+        "mov.b128 {%0, %1}, old;\n\t}"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(lo), "l"(hi), "l"(0ull), "r"((unsigned)__cvta_generic_to_shared(p))
+        : "memory");
+}
+
+// Two-word keys: probe groups of two 16-byte slots.  A claim writes both
+// words at once, but a plain 16-byte read may still see a slot being
+// claimed with its tail and not yet its head; a tail match with another head
+// is read again atomically (a CAS that can only fail) before it counts as a
+// different key.
+__device__ __forceinline__ int find_slot2(const Table& t, const unsigned long long ktail,
+                                          const unsigned long long head, unsigned g, unsigned ngroups) {
+    for (unsigned probe = 0; probe < 2 * kMaxGroupProbes; ++probe) {
+        unsigned long long* grp = t.tail + 4 * g;
+        const ulonglong2 a = lds_v2_volatile(grp);
+        const ulonglong2 b = lds_v2_volatile(grp + 2);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            unsigned long long ct = s ? b.x : a.x, ch = s ? b.y : a.y;
+            if (ct == 0ull) {  // empty (or still being claimed): try to claim it
+                unsigned long long ot, oh;
+                cas128_shared(grp + 2 * s, ktail, head, ot, oh);
+                if (ot == 0ull && oh == 0ull) return (int)(2 * g + s);
+                ct = ot;
+                ch = oh;
+            }
+            if (ct != ktail) continue;
+            if (ch != head) {
+                unsigned long long ot, oh;
+                cas128_shared(grp + 2 * s, 0ull, 0ull, ot, oh);  // the slot is claimed: no change, exact read
+                if (ot != ktail || oh != head) continue;
+            }
+            return (int)(2 * g + s);
+        }
+        g = g + 1 == ngroups ? 0 : g + 1;
+    }
+    return -1;
+}
+
 template <int W>
 __device__ __forceinline__ void insert_record(const Table& t, const unsigned long long (&rec)[W], unsigned ngroups,
                                               unsigned* s_flags) {
@@ -130,7 +206,8 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
     const unsigned hsh = (unsigned)((zl * 0x9E3779B97F4A7C15ull) >> 32);
     unsigned g = (unsigned)(((unsigned long long)hsh * ngroups) >> 32);
     int found = -1;
-    for (unsigned probe = 0; probe < kMaxGroupProbes && found < 0; ++probe) {
+    if (W == 2) found = find_slot2(t, ktail, rec[0], g, ngroups);
+    for (unsigned probe = 0; W != 2 && probe < kMaxGroupProbes && found < 0; ++probe) {
         unsigned long long* grp = t.tail + 4 * g;
         const ulonglong2 a = lds_v2_volatile(grp);
         const ulonglong2 b = lds_v2_volatile(grp + 2);
@@ -183,9 +260,10 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
 }
 
 // Clears slots [0, cap) of the table (all threads of the CTA).
+template <int W>
 __device__ __forceinline__ void clear_slots(const Table& t, unsigned cap) {
     for (unsigned s = threadIdx.x; s < cap; s += kLeafThreads) {
-        t.tail[s] = 0ull;
+        clear_key<W>(t, s);
 #pragma unroll
         for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * t.stride + s] = 0u;
     }
@@ -204,7 +282,7 @@ __device__ __forceinline__ void sweep_table(const Job& j, const Table& t, const 
     unsigned* mylist = t.list + s0;
     unsigned count = 0;
     for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
-        const unsigned long long tl = t.tail[s];
+        const unsigned long long tl = slot_tail<W>(t, s);
         const unsigned p0 = t.lanes[s], p1 = t.lanes[cap_max + s], p2 = t.lanes[2 * cap_max + s];
         const unsigned c = (p0 & 0xFFFFu) + (p0 >> 16) + (p1 & 0xFFFFu) + (p1 >> 16) + (p2 & 0xFFFFu);
         const bool ok = tl != 0ull && c >= j.min_count;
@@ -213,7 +291,7 @@ __device__ __forceinline__ void sweep_table(const Job& j, const Table& t, const 
         if (ok) {
             mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
         } else {
-            t.tail[s] = 0ull;
+            clear_key<W>(t, s);
 #pragma unroll
             for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
         }
@@ -226,14 +304,14 @@ __device__ __forceinline__ void sweep_table(const Job& j, const Table& t, const 
     for (unsigned i = lane; i < count; i += 32) {
         const unsigned s = mylist[i];
         const unsigned long long pos = wbase + i;
-        const unsigned long long tl = t.tail[s];
+        const unsigned long long tl = slot_tail<W>(t, s);
         unsigned pl[kLanePlanes];
 #pragma unroll
         for (unsigned p = 0; p < kLanePlanes; ++p) pl[p] = t.lanes[p * cap_max + s];
         unsigned long long key[W];
 #pragma unroll
-        for (int w = 0; w < W - 1; ++w) key[w] = t.heads[(size_t)w * cap_max + s];
-        t.tail[s] = 0ull;
+        for (int w = 0; w < W - 1; ++w) key[w] = slot_head<W>(t, w, s);
+        clear_key<W>(t, s);
 #pragma unroll
         for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
         if (pos >= j.out_cap) {
@@ -283,13 +361,13 @@ __device__ __forceinline__ unsigned count_in_ranges(const Job& j, const Table& t
             for (int w = 0; w < W; ++w) rec[w] = src[i * W + w];
             if (((unsigned)((rec[W - 1] >> 6) >> shift) & rmask) != rs) continue;
             ++rwin;
-            if (!*(volatile unsigned*)s_flags) insert_record<W>(t, rec, cap / 4, s_flags);
+            if (!*(volatile unsigned*)s_flags) insert_record<W>(t, rec, groups_of<W>(cap), s_flags);
         }
         __syncthreads();
         const unsigned flags = *(volatile unsigned*)s_flags;
         if (flags == kLeafFull && rb < max_rb) {  // split the range in two
             if (threadIdx.x == 0 && rb == 0) atomicAdd(j.stats + 3, 1ull);
-            clear_slots(t, cap);
+            clear_slots<W>(t, cap);
             __syncthreads();
             if (threadIdx.x == 0) *s_flags = 0;
             __syncthreads();
@@ -307,7 +385,7 @@ __device__ __forceinline__ unsigned count_in_ranges(const Job& j, const Table& t
                     else set_status(j, ST_FALLBACK_FULL);
                 }
             }
-            clear_slots(t, cap);
+            clear_slots<W>(t, cap);
         } else {
             windows += rwin;
             sweep_table<W>(j, t, li, cap, *distinct);
@@ -348,7 +426,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_split_kernel(const Job* 
         const unsigned n_split = *(volatile unsigned*)j.split_n;
         if (blockIdx.x >= n_split) continue;
         if (!init) {
-            clear_slots(t, cap_max);
+            clear_slots<W>(t, cap_max);
             if (threadIdx.x == 0) s_flags = 0;
             __syncthreads();
             init = true;
@@ -388,7 +466,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
     t.lanes = reinterpret_cast<unsigned*>(t.heads + (size_t)(W - 1) * cap_max);
     t.list = t.lanes + (size_t)kLanePlanes * cap_max;
     for (unsigned s = threadIdx.x; s < cap_max; s += kLeafThreads) {
-        t.tail[s] = 0ull;
+        clear_key<W>(t, s);
 #pragma unroll
         for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
     }
@@ -452,7 +530,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
         const unsigned long long n = li.n;
         const unsigned long long want = ((n * j.table_ratio_num) >> 16) + 512;
         const unsigned cap = (unsigned)(want < cap_max ? ((want + 511) & ~511ull) : cap_max);
-        const unsigned ngroups = cap / 4;
+        const unsigned ngroups = groups_of<W>(cap);
         for (unsigned long long first = 0; first < n; first += B) {
             if (first) load_batch<W>(li, first, batch);
 #pragma unroll
@@ -488,7 +566,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
                 }
             }
             for (unsigned s = s0 + lane; s < s0 + per; s += 32) {  // leave the table clean
-                t.tail[s] = 0ull;
+                clear_key<W>(t, s);
 #pragma unroll
                 for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
             }
@@ -498,7 +576,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
             unsigned* mylist = t.list + s0;
             unsigned count = 0;
             for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
-                const unsigned long long tl = t.tail[s];
+                const unsigned long long tl = slot_tail<W>(t, s);
                 const unsigned p0 = t.lanes[s], p1 = t.lanes[cap_max + s], p2 = t.lanes[2 * cap_max + s];
                 const unsigned c = (p0 & 0xFFFFu) + (p0 >> 16) + (p1 & 0xFFFFu) + (p1 >> 16) + (p2 & 0xFFFFu);
                 const bool ok = tl != 0ull && c >= j.min_count;
@@ -507,7 +585,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
                 if (ok) {
                     mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
                 } else {
-                    t.tail[s] = 0ull;
+                    clear_key<W>(t, s);
 #pragma unroll
                     for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
                 }
@@ -520,14 +598,14 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
             for (unsigned i = lane; i < count; i += 32) {
                 const unsigned s = mylist[i];
                 const unsigned long long pos = wbase + i;
-                const unsigned long long tl = t.tail[s];
+                const unsigned long long tl = slot_tail<W>(t, s);
                 unsigned pl[kLanePlanes];
 #pragma unroll
                 for (unsigned p = 0; p < kLanePlanes; ++p) pl[p] = t.lanes[p * cap_max + s];
                 unsigned long long key[W];
 #pragma unroll
-                for (int w = 0; w < W - 1; ++w) key[w] = t.heads[(size_t)w * cap_max + s];
-                t.tail[s] = 0ull;
+                for (int w = 0; w < W - 1; ++w) key[w] = slot_head<W>(t, w, s);
+                clear_key<W>(t, s);
 #pragma unroll
                 for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
                 if (pos >= j.out_cap) {
