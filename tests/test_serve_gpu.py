@@ -105,3 +105,50 @@ def test_pooled_analysis_serves_other_readsets_at_the_same_k(readsets):
         same_result(srv.results(rid), alone(readsets[i], 21))
         srv.release(rid)
     srv.close()
+
+
+def test_threads_pipelining_staged_steps():
+    """Host threads each with their own stream, readset and analysis, as the
+    end-to-end bench runs them: reads re-packed from page-locked memory by the
+    copy engines, counting one step at a time under a lock, survivors copied
+    out by the copy engines.  Every step of every thread gives the oracle's
+    result for its own reads."""
+    import torch
+    import oracle
+    from tests.helpers import assert_same
+    samples = [synth.generate(synth.METAGENOME_2G.scaled(6_000 + 1_000 * i, seed=40 + i)) for i in range(3)]
+    want = [oracle.run(s.bases, s.quals, s.offsets, oracle.Params(k=31)) for s in samples]
+    lock, errors = threading.Lock(), []
+
+    def lane(i):
+        try:
+            st = torch.cuda.Stream()
+            s = samples[i]
+            b, q, o = (torch.from_numpy(a).pin_memory() for a in (s.bases, s.quals, s.offsets.view(np.int64)))
+            rs = pkg.ReadSet(b[:150].clone(), q[:150].clone(), torch.tensor([0, 150], dtype=torch.int64), stream=st,
+                             staged=True)
+            ka = pkg.KmerAnalysis(31, stream=st)
+            for step in range(3):
+                rs.pack(b, q, o, stream=st, staged=True)
+                with lock:
+                    ka.reset()
+                    ka.submit(rs)
+                    v = pkg.kmer_analysis_query(ka.handle)
+                n = int(v.n)
+                keys, cnt = np.empty((n, 1), np.uint64), np.empty(n, np.uint32)
+                ext, cls = np.empty((n, 8), np.uint32), np.empty((n, 2), np.uint8)
+                pkg.kmer_analysis_copy_results(ka.handle, keys.ctypes.data, cnt.ctypes.data, ext.ctypes.data,
+                                               cls.ctypes.data, n)
+                got = pkg.Result(31, keys, cnt, ext, cls, int(v.windows), int(v.distinct))
+                assert_same(got, want[i], f"thread {i} step {step}")
+            ka.close()
+            rs.close()
+        except Exception as e:  # reported in the main thread
+            errors.append(e)
+
+    ths = [threading.Thread(target=lane, args=(i,)) for i in range(3)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert not errors, errors
