@@ -419,7 +419,12 @@ def run_ours(args):
             ln["windows"] += int(vv.windows)
             ln["d2h"] += int(vv.n) * (8 * W + 4 + 32 + 2)
 
-        def run_lane(ln, n, stg):
+        cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+
+        def run_lane(ln, n, stg, idx=None):
+            # each pipelining thread keeps a core of its own (it spins on its copies' events)
+            if idx is not None and len(cores) > n_thr + 1:
+                os.sched_setaffinity(0, {cores[1 + idx]})
             torch.cuda.set_device(dev)
             for _ in range(n):
                 e2e_step(ln, stg)
@@ -442,7 +447,7 @@ def run_ours(args):
             ln["windows"] = ln["d2h"] = 0
         barrier()
         t0 = time.perf_counter()
-        ths = [threading.Thread(target=run_lane, args=(lanes[i], (e2e_steps + n_thr - 1 - i) // n_thr, staged))
+        ths = [threading.Thread(target=run_lane, args=(lanes[i], (e2e_steps + n_thr - 1 - i) // n_thr, staged, i))
                for i in range(n_thr)]
         for th in ths:
             th.start()
