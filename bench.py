@@ -422,9 +422,11 @@ def run_ours(args):
         cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
 
         def run_lane(ln, n, stg, idx=None):
-            # each pipelining thread keeps a core of its own (it spins on its copies' events)
-            if idx is not None and len(cores) > n_thr + 1:
-                os.sched_setaffinity(0, {cores[1 + idx]})
+            # each pipelining thread keeps a core of its own (it spins on its copies' events);
+            # the ranks of one node take disjoint cores
+            local_world = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+            if idx is not None and len(cores) >= local_world * (n_thr + 1):
+                os.sched_setaffinity(0, {cores[local * (n_thr + 1) + 1 + idx]})
             torch.cuda.set_device(dev)
             for _ in range(n):
                 e2e_step(ln, stg)
