@@ -30,6 +30,8 @@
  *    in integers; no extension at all is DEAD_END; a tie for most common is
  *    FORK.  ext_mode 1 (static, Sec. II-B): bases with tally >= t_ext are
  *    high-quality extensions; exactly one is UNIQUE, none DEAD_END, more FORK.
+ *    The paper calls a base high quality when it is seen more than t_hq
+ *    times; t_ext is that threshold written inclusively, t_ext = t_hq + 1.
  *
  * Keys are returned 2 bits per base (A=0, C=1, G=2, T=3), first base most
  * significant, in W = ceil(2k/64) 64-bit words; word 0 is the most
@@ -379,15 +381,19 @@ int kmer_server_destroy(kmer_server_t *s);
  * on each device where the library is used and held until the process exits;
  * it bounds the input: the reads may span at most 393216 bases for k <= 63
  * and 196608 bases for k >= 65 (larger inputs return INVALID_ARG before any
- * work).  The caller passes the output arrays (device pointers, `capacity`
- * k-mers, layout of kmer_result_view); *n_out receives the number of
- * survivors, and if it exceeds `capacity` the call returns INVALID_ARG with
- * the surplus not written.  Synchronises `cuda_stream`.  The first call on a
- * device also looks up the scratch array's device address, so make that
- * first call before any stream capture.  Every call reuses the same array
- * (each call clears it first): calls that overlap on the GPU, from several
- * streams or threads, race and must be serialised by the caller.  Errors:
- * INVALID_ARG, NO_DEVICE, TABLE_FULL, COUNTER_OVERFLOW, TIMEOUT, CUDA. */
+ * work).  Offsets must not decrease: a read whose offsets decrease or leave
+ * [offsets[0], offsets[n_reads]] is skipped without reading its bases, and
+ * the call returns INVALID_ARG.  The caller passes the output arrays (device
+ * pointers, `capacity` k-mers, layout of kmer_result_view); *n_out receives
+ * the number of survivors, and if it exceeds `capacity` the call returns
+ * INVALID_ARG with the surplus not written.  Synchronises `cuda_stream`
+ * (it reads two offsets and its counters back to the host).  The first call
+ * on each device, and in each CUDA context, also looks up the scratch
+ * array's device address, so make that first call before any stream capture
+ * begins.  Every call reuses the same array (each call clears it first):
+ * calls that overlap on the GPU, from several streams or threads, race and
+ * must be serialised by the caller.  Errors: INVALID_ARG, NO_DEVICE,
+ * TABLE_FULL, COUNTER_OVERFLOW, TIMEOUT, CUDA. */
 int kmer_analysis_run_noalloc(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
                               const kmer_analysis_params *p, uint64_t *keys, uint32_t *count, uint32_t *ext,
                               uint8_t *cls, uint64_t capacity, uint64_t *n_out, void *cuda_stream);

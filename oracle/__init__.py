@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
         return _LIB
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB + f".{os.getpid()}.tmp"
-    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, src], check=True)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", tmp, src], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -67,6 +67,10 @@ def _load():
             lib.oracle_kmer_analysis.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(_Params),
                                                  ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_Result)]
             lib.oracle_kmer_analysis.restype = ctypes.c_int
+            lib.oracle_kmer_analysis_threads.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(_Params),
+                                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                         ctypes.c_uint32, ctypes.POINTER(_Result)]
+            lib.oracle_kmer_analysis_threads.restype = ctypes.c_int
             lib.oracle_free.argtypes = [ctypes.POINTER(_Result)]
             lib.oracle_free.restype = None
             lib.oracle_fnv1a.argtypes = [ctypes.c_char_p, ctypes.c_uint64]
@@ -124,26 +128,22 @@ def _as_u8(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.uint8)
 
 
-def run(bases, quals, offsets, params: Params, shard: int = 0, n_shards: int = 1) -> Result:
-    """Run the oracle on reads given in the flat layout (bases, quals, offsets)."""
-    lib = _load()
+def _inputs(bases, quals, offsets):
     b = _as_u8(bases)
     q = _as_u8(quals)
     o = np.ascontiguousarray(offsets, dtype=np.uint64)
     n_reads = len(o) - 1
     if n_reads < 0 or (n_reads and int(o[-1]) > len(b)) or len(q) < len(b):
         raise ValueError("offsets do not match the base/quality buffers")
-    res = _Result()
-    cp = params._c()
-    rc = lib.oracle_kmer_analysis(ctypes.c_void_p(b.ctypes.data if len(b) else 0),
-                                  ctypes.c_void_p(q.ctypes.data if len(q) else 0),
-                                  ctypes.c_void_p(o.ctypes.data), n_reads, ctypes.byref(cp),
-                                  shard, n_shards, ctypes.byref(res))
+    return b, q, o, n_reads
+
+
+def _collect(lib, res, rc, k) -> Result:
     if rc:
         lib.oracle_free(ctypes.byref(res))
         raise ValueError(f"oracle rejected its arguments (status {rc})")
     try:
-        n, k = int(res.n), params.k
+        n = int(res.n)
         keys = np.frombuffer(ctypes.string_at(res.keys, n * k), dtype=f"S{k}").copy() if n else \
             np.empty(0, dtype=f"S{k}")
         count = np.frombuffer(ctypes.string_at(res.count, 8 * n), dtype=np.uint64).copy()
@@ -152,6 +152,43 @@ def run(bases, quals, offsets, params: Params, shard: int = 0, n_shards: int = 1
         return Result(keys, count, ext, cls, int(res.windows), int(res.distinct))
     finally:
         lib.oracle_free(ctypes.byref(res))
+
+
+def run(bases, quals, offsets, params: Params, shard: int = 0, n_shards: int = 1) -> Result:
+    """Run the oracle on reads given in the flat layout (bases, quals, offsets)."""
+    lib = _load()
+    b, q, o, n_reads = _inputs(bases, quals, offsets)
+    res = _Result()
+    cp = params._c()
+    rc = lib.oracle_kmer_analysis(ctypes.c_void_p(b.ctypes.data if len(b) else 0),
+                                  ctypes.c_void_p(q.ctypes.data if len(q) else 0),
+                                  ctypes.c_void_p(o.ctypes.data), n_reads, ctypes.byref(cp),
+                                  shard, n_shards, ctypes.byref(res))
+    return _collect(lib, res, rc, params.k)
+
+
+def run_threads(bases, quals, offsets, params: Params, shard_lo: int = 0, shard_hi: int = 1, n_shards: int = 1,
+                threads: int = 1) -> Result:
+    """The keys of shards [shard_lo, shard_hi) of n_shards (all keys with the
+    defaults), the reads split into `threads` ranges counted in parallel and
+    the partial maps summed before the filter (one result, ascending)."""
+    lib = _load()
+    b, q, o, n_reads = _inputs(bases, quals, offsets)
+    res = _Result()
+    cp = params._c()
+    rc = lib.oracle_kmer_analysis_threads(ctypes.c_void_p(b.ctypes.data if len(b) else 0),
+                                          ctypes.c_void_p(q.ctypes.data if len(q) else 0),
+                                          ctypes.c_void_p(o.ctypes.data), n_reads, ctypes.byref(cp),
+                                          shard_lo, shard_hi, n_shards, max(1, threads), ctypes.byref(res))
+    return _collect(lib, res, rc, params.k)
+
+
+def host_threads() -> int:
+    """Cores this process may run on (all host cores unless restricted)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return max(1, os.cpu_count() or 1)
 
 
 def run_reads(reads, params: Params) -> Result:

@@ -33,13 +33,20 @@
  *
  * Sharded mode (n_shards > 1) keeps only keys whose FNV-1a 64-bit hash of the
  * key string is congruent to `shard`; it is the same definition restricted to
- * a subset of keys, so that large inputs fit in host memory.
+ * a subset of keys, so that large inputs fit in host memory.  The threaded
+ * form (oracle_kmer_analysis_threads) keeps a range of shards, splits the
+ * reads into contiguous ranges counted by separate threads into maps of
+ * their own, and adds the maps together before filtering: the counts and
+ * tallies are sums over windows, and update-only inserts commute
+ * (Sec. II-A, use case 1).
  */
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <string>
+#include <thread>
 #include <vector>
 
 extern "C" {
@@ -174,6 +181,46 @@ void add_window(Rec &rec, int left, int right) {
     if (right >= 0) rec.ext[1][right] += 1;
 }
 
+using Entry = std::pair<const std::string, Rec>;
+
+// Keys seen at least min_count times, from `all` (every distinct key,
+// ascending), with their counts, tallies and classes.
+int write_result(const std::vector<const Entry *> &all, uint64_t windows, const oracle_params &p,
+                 oracle_result *out) {
+    const size_t k = p.k;
+    std::vector<const Entry *> keep;
+    for (const Entry *kv : all)
+        if (kv->second.count >= p.min_count) keep.push_back(kv);
+    const uint64_t n = keep.size();
+    out->n = n;
+    out->windows = windows;
+    out->distinct = all.size();
+    out->keys = (char *)std::malloc(n * k + 1);
+    out->count = (uint64_t *)std::malloc(sizeof(uint64_t) * (n + 1));
+    out->ext = (uint64_t *)std::malloc(sizeof(uint64_t) * (8 * n + 1));
+    out->cls = (uint8_t *)std::malloc(2 * n + 1);
+    if (!out->keys || !out->count || !out->ext || !out->cls) return -2;
+    for (uint64_t j = 0; j < n; ++j) {
+        const std::string &key = keep[j]->first;
+        const Rec &rec = keep[j]->second;
+        std::memcpy(out->keys + j * k, key.data(), k);
+        out->count[j] = rec.count;
+        for (int s = 0; s < 2; ++s)
+            for (int b = 0; b < 4; ++b) out->ext[8 * j + 4 * s + b] = rec.ext[s][b];
+        out->cls[2 * j + 0] = classify(rec.ext[0], rec.count, p);
+        out->cls[2 * j + 1] = classify(rec.ext[1], rec.count, p);
+    }
+    return 0;
+}
+
+int write_result(const std::map<std::string, Rec> &M, uint64_t windows, const oracle_params &p,
+                 oracle_result *out) {
+    std::vector<const Entry *> all;
+    all.reserve(M.size());
+    for (const auto &kv : M) all.push_back(&kv);
+    return write_result(all, windows, p, out);
+}
+
 }  // namespace
 
 extern "C" int oracle_kmer_analysis(const char *bases, const uint8_t *quals, const uint64_t *offsets,
@@ -194,29 +241,81 @@ extern "C" int oracle_kmer_analysis(const char *bases, const uint8_t *quals, con
             add_window(M[c], left, right);
         });
     }
-    std::vector<const std::pair<const std::string, Rec> *> keep;
-    for (const auto &kv : M)
-        if (kv.second.count >= p->min_count) keep.push_back(&kv);
-    const uint64_t n = keep.size();
-    out->n = n;
-    out->windows = windows;
-    out->distinct = M.size();
-    out->keys = (char *)std::malloc(n * k + 1);
-    out->count = (uint64_t *)std::malloc(sizeof(uint64_t) * (n + 1));
-    out->ext = (uint64_t *)std::malloc(sizeof(uint64_t) * (8 * n + 1));
-    out->cls = (uint8_t *)std::malloc(2 * n + 1);
-    if (!out->keys || !out->count || !out->ext || !out->cls) return -2;
-    for (uint64_t j = 0; j < n; ++j) {
-        const std::string &key = keep[j]->first;
-        const Rec &rec = keep[j]->second;
-        std::memcpy(out->keys + j * k, key.data(), k);
-        out->count[j] = rec.count;
-        for (int s = 0; s < 2; ++s)
-            for (int b = 0; b < 4; ++b) out->ext[8 * j + 4 * s + b] = rec.ext[s][b];
-        out->cls[2 * j + 0] = classify(rec.ext[0], rec.count, *p);
-        out->cls[2 * j + 1] = classify(rec.ext[1], rec.count, *p);
+    return write_result(M, windows, *p, out);
+}
+
+/* The definition restricted to the keys whose FNV-1a hash modulo n_shards
+ * lies in [shard_lo, shard_hi), with the reads split into `threads`
+ * contiguous ranges counted in parallel.  Each thread fills maps of its own,
+ * one per merge group (the hash divided by n_shards, modulo `threads`, so
+ * that every key has one group); then thread g adds up group g's maps key by
+ * key (counts and tallies are sums over windows), and the groups, disjoint
+ * and each ascending, are merged into one ascending list before the count
+ * filter and the classes, which see the totals. */
+extern "C" int oracle_kmer_analysis_threads(const char *bases, const uint8_t *quals, const uint64_t *offsets,
+                                            uint64_t n_reads, const oracle_params *p, uint32_t shard_lo,
+                                            uint32_t shard_hi, uint32_t n_shards, uint32_t threads,
+                                            oracle_result *out) {
+    if (!p || !out || (n_reads && (!bases || !quals || !offsets))) return -1;
+    if (p->k == 0 || n_shards == 0 || shard_lo >= shard_hi || shard_hi > n_shards || threads == 0) return -1;
+    if (p->ext_mode == 0 && p->err_den == 0) return -1;
+    std::memset(out, 0, sizeof(*out));
+    const size_t k = p->k;
+    const uint32_t T = threads;
+    // part[t][g]: keys of merge group g seen by thread t
+    std::vector<std::vector<std::map<std::string, Rec>>> part(T, std::vector<std::map<std::string, Rec>>(T));
+    std::vector<uint64_t> part_windows(T, 0);
+    std::vector<std::thread> pool;
+    for (uint32_t t = 0; t < T; ++t) {
+        const uint64_t r0 = n_reads * t / T, r1 = n_reads * (t + 1) / T;
+        pool.emplace_back([&, t, r0, r1]() {
+            for (uint64_t r = r0; r < r1; ++r) {
+                const std::string read(bases + offsets[r], bases + offsets[r + 1]);
+                walk_read(read, quals + offsets[r], k, *p, [&](const std::string &c, int left, int right) {
+                    const uint64_t h = fnv1a(c);
+                    const uint64_t sh = h % n_shards;
+                    if (sh < shard_lo || sh >= shard_hi) return;
+                    ++part_windows[t];
+                    add_window(part[t][(h / n_shards) % T][c], left, right);
+                });
+            }
+        });
     }
-    return 0;
+    for (auto &th : pool) th.join();
+    pool.clear();
+    std::vector<std::map<std::string, Rec>> group(T);
+    for (uint32_t g = 0; g < T; ++g) {
+        pool.emplace_back([&, g]() {
+            for (uint32_t t = 0; t < T; ++t) {
+                for (const auto &kv : part[t][g]) {
+                    Rec &rec = group[g][kv.first];
+                    rec.count += kv.second.count;
+                    for (int s = 0; s < 2; ++s)
+                        for (int b = 0; b < 4; ++b) rec.ext[s][b] += kv.second.ext[s][b];
+                }
+                std::map<std::string, Rec>().swap(part[t][g]);
+            }
+        });
+    }
+    for (auto &th : pool) th.join();
+    uint64_t windows = 0, distinct = 0;
+    for (uint32_t t = 0; t < T; ++t) windows += part_windows[t];
+    for (uint32_t g = 0; g < T; ++g) distinct += group[g].size();
+    // k-way merge of the groups into ascending order
+    using It = std::map<std::string, Rec>::const_iterator;
+    auto later = [](const std::pair<It, It> &a, const std::pair<It, It> &b) { return b.first->first < a.first->first; };
+    std::priority_queue<std::pair<It, It>, std::vector<std::pair<It, It>>, decltype(later)> heads(later);
+    for (uint32_t g = 0; g < T; ++g)
+        if (!group[g].empty()) heads.push({group[g].cbegin(), group[g].cend()});
+    std::vector<const Entry *> all;
+    all.reserve(distinct);
+    while (!heads.empty()) {
+        auto h = heads.top();
+        heads.pop();
+        all.push_back(&*h.first);
+        if (++h.first != h.second) heads.push(h);
+    }
+    return write_result(all, windows, *p, out);
 }
 
 extern "C" void oracle_free(oracle_result *r) {

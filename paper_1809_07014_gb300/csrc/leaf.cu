@@ -572,60 +572,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(const Job* __rest
             }
         } else {
             if (threadIdx.x == 0) windows += n;
-            // ------------------------------------------------------ sweep (per warp)
-            unsigned* mylist = t.list + s0;
-            unsigned count = 0;
-            for (unsigned s = s0 + lane; s < s0 + per; s += 32) {
-                const unsigned long long tl = slot_tail<W>(t, s);
-                const unsigned p0 = t.lanes[s], p1 = t.lanes[cap_max + s], p2 = t.lanes[2 * cap_max + s];
-                const unsigned c = (p0 & 0xFFFFu) + (p0 >> 16) + (p1 & 0xFFFFu) + (p1 >> 16) + (p2 & 0xFFFFu);
-                const bool ok = tl != 0ull && c >= j.min_count;
-                distinct += tl != 0ull ? 1 : 0;
-                const unsigned m = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    mylist[count + __popc(m & ((1u << lane) - 1u))] = s;
-                } else {
-                    clear_key<W>(t, s);
-#pragma unroll
-                    for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
-                }
-                count += __popc(m);
-            }
-            __syncwarp();
-            unsigned long long wbase = 0;
-            if (lane == 0 && count) wbase = atomicAdd(j.out_n, (unsigned long long)count);
-            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-            for (unsigned i = lane; i < count; i += 32) {
-                const unsigned s = mylist[i];
-                const unsigned long long pos = wbase + i;
-                const unsigned long long tl = slot_tail<W>(t, s);
-                unsigned pl[kLanePlanes];
-#pragma unroll
-                for (unsigned p = 0; p < kLanePlanes; ++p) pl[p] = t.lanes[p * cap_max + s];
-                unsigned long long key[W];
-#pragma unroll
-                for (int w = 0; w < W - 1; ++w) key[w] = slot_head<W>(t, w, s);
-                clear_key<W>(t, s);
-#pragma unroll
-                for (unsigned p = 0; p < kLanePlanes; ++p) t.lanes[p * cap_max + s] = 0u;
-                if (pos >= j.out_cap) {
-                    set_status(j, ST_OUT_OVERFLOW);
-                    continue;
-                }
-                const unsigned nl[4] = {pl[0] & 0xFFFFu, pl[0] >> 16, pl[1] & 0xFFFFu, pl[1] >> 16};
-                const unsigned nr[4] = {pl[2] >> 16, pl[3] & 0xFFFFu, pl[3] >> 16, pl[4] & 0xFFFFu};
-                const unsigned c = nl[0] + nl[1] + nl[2] + nl[3] + (pl[2] & 0xFFFFu);
-                const unsigned long long z = record_z(j.g, j.pass, li.bucket, tl);
-                key[W - 1] = z_to_tail<W>(z, key, j.g.bt);
-#pragma unroll
-                for (int w = 0; w < W; ++w) j.out_keys[pos * W + w] = key[w];
-                j.out_count[pos] = c;
-                uint4* eo = reinterpret_cast<uint4*>(j.out_ext + pos * 8);
-                eo[0] = make_uint4(nl[0], nl[1], nl[2], nl[3]);
-                eo[1] = make_uint4(nr[0], nr[1], nr[2], nr[3]);
-                reinterpret_cast<uchar2*>(j.out_cls)[pos] =
-                    make_uchar2(classify_side(nl, c, j), classify_side(nr, c, j));
-            }
+            sweep_table<W>(j, t, li, cap, distinct);  // filter, classify, compact (per warp)
         }
         if (threadIdx.x == 0) s_flags = 0;
         __syncthreads();  // the clean table is reused by the next leaf

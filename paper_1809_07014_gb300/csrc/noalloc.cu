@@ -12,10 +12,12 @@
 // inserted into one open-addressing table, then the table swept), reading
 // the ASCII bases and qualities directly, so that no packed copy is needed.
 // The table lives in the static array, which bounds the input size.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kmer_analysis.h"
@@ -30,10 +32,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 struct NaCounters {
     unsigned long long out_n;
-    unsigned long long windows;
-    unsigned long long distinct;
     unsigned int status;
 };
+
+// A read whose offsets decrease or leave [offsets[0], offsets[n_reads]]:
+// skipped without touching its bases, and the call returns INVALID_ARG.
+constexpr unsigned kNaBadOffsets = 1u << 8;
 
 constexpr unsigned long long kNaOcc = 1ull << 63, kNaPub = 1ull << 62;
 constexpr unsigned kNaSpinLimit = 1u << 22;
@@ -118,7 +122,8 @@ template <int W>
 __global__ void __launch_bounds__(256) noalloc_insert_kernel(const char* __restrict__ bases,
                                                             const unsigned char* __restrict__ quals,
                                                             const unsigned long long* __restrict__ offsets,
-                                                            unsigned long long n_reads, unsigned k,
+                                                            unsigned long long n_reads, unsigned long long span0,
+                                                            unsigned long long span1, unsigned k,
                                                             unsigned qual_offset, unsigned qual_threshold,
                                                             unsigned char* scratch) {
     NaCounters* cnt = reinterpret_cast<NaCounters*>(scratch);
@@ -128,9 +133,14 @@ __global__ void __launch_bounds__(256) noalloc_insert_kernel(const char* __restr
     const unsigned bt = W == 1 ? 2 * k : 64;
     const unsigned long long topmask = low_mask(hb);
     const unsigned long long r = blockIdx.x * 256ull + threadIdx.x;
-    unsigned long long windows = 0;
     if (r < n_reads) {
-        const unsigned long long a = offsets[r], L = offsets[r + 1] - a;
+        const unsigned long long a = offsets[r], e = offsets[r + 1];
+        // only the span [offsets[0], offsets[n_reads]) was checked by the host
+        if (a < span0 || e < a || e > span1) {
+            atomicOr(&cnt->status, kNaBadOffsets);
+            return;
+        }
+        const unsigned long long L = e - a;
         unsigned long long fwd[W], rc[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) { fwd[w] = 0; rc[w] = 0; }
@@ -171,7 +181,6 @@ __global__ void __launch_bounds__(256) noalloc_insert_kernel(const char* __restr
                 }
                 const unsigned long long z = key_to_z<W>(key, bt);
                 if (!na_insert<W>(table, cap, key, z, lc, rcd, cnt)) break;
-                ++windows;
             }
             if (t < L) {
                 out = (unsigned)(fwd[0] >> (hb - 2)) & 3u;
@@ -188,7 +197,6 @@ __global__ void __launch_bounds__(256) noalloc_insert_kernel(const char* __restr
             }
         }
     }
-    if (windows) atomicAdd(&cnt->windows, windows);
 }
 
 template <int W>
@@ -200,7 +208,6 @@ __global__ void __launch_bounds__(256) noalloc_sweep_kernel(unsigned char* scrat
     const NaEntry<W>* table = reinterpret_cast<const NaEntry<W>*>(scratch + kNoAllocHeader);
     const unsigned long long cap = na_slots(W);
     const int lane = threadIdx.x & 31;
-    unsigned long long distinct = 0;
     for (unsigned long long base = blockIdx.x * 256ull + (threadIdx.x & ~31u); base < cap;
          base += (unsigned long long)gridDim.x * 256) {
         const unsigned long long s = base + lane;
@@ -208,7 +215,6 @@ __global__ void __launch_bounds__(256) noalloc_sweep_kernel(unsigned char* scrat
         const unsigned long long k0 = s < cap ? e->key[0] : 0ull;
         const unsigned c = k0 ? e->count : 0u;
         const bool ok = k0 != 0ull && c >= min_count;
-        distinct += k0 ? 1 : 0;
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         unsigned long long wbase = 0;
         if (lane == 0 && m) wbase = atomicAdd(&cnt->out_n, (unsigned long long)__popc(m));
@@ -230,40 +236,61 @@ __global__ void __launch_bounds__(256) noalloc_sweep_kernel(unsigned char* scrat
             }
         }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
-    if (lane == 0 && distinct) atomicAdd(&cnt->distinct, distinct);
 }
 
-// Device address of the static array, looked up once per device.
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+// Device address of the static array, looked up once per device and CUDA
+// context: a module's symbol address belongs to the context that loaded it,
+// so a caller that runs this function under a context of its own, or after
+// cudaDeviceReset, gets the address in the context current at the call.
+struct ScratchAddr {
+    int dev;
+    CUcontext ctx;
+    unsigned char* ptr;
+};
+std::vector<ScratchAddr> g_scratch_addrs;
 std::mutex g_scratch_mu;
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
 
 int scratch_for_device(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= kMaxDevices) return KMER_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        // the host-side name of the array is only a stand-in: ask the runtime for its device address
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    if (!g_ctx_get_current) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
             cudaGetLastError();
             return KMER_ERR_CUDA;
         }
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
     }
-    *out = g_scratch_ptr[dev];
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return KMER_ERR_NO_DEVICE;
+    for (const ScratchAddr& a : g_scratch_addrs)
+        if (a.dev == dev && a.ctx == ctx) {
+            *out = a.ptr;
+            return KMER_OK;
+        }
+    void* p = nullptr;
+    // the host-side name of the array is only a stand-in: ask the runtime for its device address
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return KMER_ERR_CUDA;
+    }
+    g_scratch_addrs.push_back({dev, ctx, static_cast<unsigned char*>(p)});
+    *out = static_cast<unsigned char*>(p);
     return KMER_OK;
 }
 
 template <int W>
 cudaError_t launch_noalloc(const char* bases, const uint8_t* quals, const uint64_t* offsets, uint64_t n_reads,
-                           const kmer_analysis_params* p, unsigned char* scratch, uint64_t* keys, uint32_t* count,
-                           uint32_t* ext, uint8_t* cls, uint64_t capacity, cudaStream_t s) {
+                           const unsigned long long (&span)[2], const kmer_analysis_params* p,
+                           unsigned char* scratch, uint64_t* keys, uint32_t* count, uint32_t* ext, uint8_t* cls,
+                           uint64_t capacity, cudaStream_t s) {
     if (n_reads) {
         noalloc_insert_kernel<W><<<(unsigned)((n_reads + 255) / 256), 256, 0, s>>>(
-            bases, quals, reinterpret_cast<const unsigned long long*>(offsets), n_reads, p->k, p->qual_offset,
-            p->qual_threshold, scratch);
+            bases, quals, reinterpret_cast<const unsigned long long*>(offsets), n_reads, span[0], span[1], p->k,
+            p->qual_offset, p->qual_threshold, scratch);
     }
     Job cp{};
     cp.ext_mode = p->ext_mode;
@@ -323,10 +350,10 @@ extern "C" int kmer_analysis_run_noalloc(const char* bases, const uint8_t* quals
     }
     cudaError_t e;
     switch (W) {
-        case 1: e = launch_noalloc<1>(bases, quals, offsets, n_reads, p, scratch, keys, count, ext, cls, capacity, s); break;
-        case 2: e = launch_noalloc<2>(bases, quals, offsets, n_reads, p, scratch, keys, count, ext, cls, capacity, s); break;
-        case 3: e = launch_noalloc<3>(bases, quals, offsets, n_reads, p, scratch, keys, count, ext, cls, capacity, s); break;
-        default: e = launch_noalloc<4>(bases, quals, offsets, n_reads, p, scratch, keys, count, ext, cls, capacity, s); break;
+        case 1: e = launch_noalloc<1>(bases, quals, offsets, n_reads, span, p, scratch, keys, count, ext, cls, capacity, s); break;
+        case 2: e = launch_noalloc<2>(bases, quals, offsets, n_reads, span, p, scratch, keys, count, ext, cls, capacity, s); break;
+        case 3: e = launch_noalloc<3>(bases, quals, offsets, n_reads, span, p, scratch, keys, count, ext, cls, capacity, s); break;
+        default: e = launch_noalloc<4>(bases, quals, offsets, n_reads, span, p, scratch, keys, count, ext, cls, capacity, s); break;
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -338,6 +365,7 @@ extern "C" int kmer_analysis_run_noalloc(const char* bases, const uint8_t* quals
         cudaGetLastError();
         return KMER_ERR_CUDA;
     }
+    if (c.status & kNaBadOffsets) return KMER_ERR_INVALID_ARG;  // nothing of the call is usable
     *n_out = c.out_n;
     if (c.status & ST_TIMEOUT) return KMER_ERR_TIMEOUT;
     if (c.status & ST_COUNTER_OVERFLOW) return KMER_ERR_COUNTER_OVERFLOW;

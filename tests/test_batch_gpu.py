@@ -154,3 +154,38 @@ def test_batch_replans_from_its_counts(samples):
     b.run()
     assert b.stats()["replans"] == 1  # the learned plan holds
     b.close()
+
+
+def test_batch_job_of_100_mbases_complete_on_hash_shards():
+    """One job of the batched workload at full size (107 Mbases, k = 33, 32
+    genomes) in a batch with smaller jobs of mixed k: its survivors in the
+    hash shards 0-3 of 16 (a quarter of the key space) equal the oracle's
+    key by key, with every count, tally and class; the other jobs equal the
+    regular path."""
+    import bench
+    from tests.helpers import fnv1a_keys, decode_keys
+    recipes = bench.batch_workload(1.0)
+    big_recipe, big_k = recipes[22]
+    assert big_recipe.n_reads * 150 >= 100_000_000 and big_k == 33
+    big = synth.generate(big_recipe, threads=oracle.host_threads())
+    small = [(sample(i, n), k) for i, (n, k) in enumerate([(4000, 21), (700, 55), (12000, 33), (2500, 21)])]
+    rsets = [pkg.ReadSet(big.bases, big.quals, big.offsets)] + [pkg.ReadSet(s.bases, s.quals, s.offsets)
+                                                               for s, _ in small]
+    ks = [big_k] + [k for _, k in small]
+    b = pkg.Batch([(r, {"k": k}) for r, k in zip(rsets, ks)])
+    b.run()
+    got = b.results(0)
+    for i in range(1, len(rsets)):
+        same_result(b.results(i), regular(rsets[i], ks[i]))
+    b.close()
+    for r in rsets:
+        r.close()
+    lo, hi, n_shards = 0, 4, 16
+    h = fnv1a_keys(decode_keys(got.keys, big_k)) % np.uint64(n_shards)
+    sel = np.nonzero((h >= lo) & (h < hi))[0]
+    want = oracle.run_threads(big.bases, big.quals, big.offsets, oracle.Params(k=big_k), lo, hi, n_shards,
+                              threads=oracle.host_threads())
+    assert len(want) > 500_000
+    part = pkg.Result(keys=got.keys[sel], count=got.count[sel], ext=got.ext[sel], cls=got.cls[sel], k=big_k,
+                      windows=want.windows, distinct=want.distinct)
+    assert_same(part, want, f"107-Mbase batch job, k={big_k}, shards {lo}-{hi - 1} of {n_shards}")

@@ -1,15 +1,19 @@
 """Full-size check on the 2-Gbase metagenome at k = 31, in the benchmark's
 launch configuration (default parameters, reads resident on the device).
 
-The oracle cannot count all 1.6 G windows in a test, so:
-  * properties that hold at any size are checked on every survivor (unique,
-    canonical keys; count >= min_count; tallies <= count; classes follow the
-    rule) and the total window count is checked against an independent
-    count of windows without N;
-  * sampled outputs are computed one by one by the oracle's key-set mode over
-    all reads: 3000 random survivors (exact count, tallies, classes) and 3000
-    canonical k-mers taken from random read windows (present on the GPU iff
-    their oracle count reaches min_count, with equal values).
+Checks:
+  * complete parity on hash shards: the oracle's threaded sharded mode counts
+    every window of all 13.3 M reads but keeps only the keys whose FNV-1a
+    hash modulo 64 is 0-3 (1/16 of the key space, about 7 M survivors), and
+    the GPU survivors with the same hash are compared with them key by key:
+    the same key set, and every count, tally and class;
+  * properties that hold at any size on every survivor (unique, canonical
+    keys; count >= min_count; tallies <= count) and the total window count
+    against an independent count of windows without N;
+  * sampled outputs computed one by one by the oracle's key-set mode over all
+    reads: 3000 random survivors of every shard and 3000 canonical k-mers
+    taken from random read windows (present on the GPU iff their oracle count
+    reaches min_count, with equal values).
 """
 import os
 
@@ -19,7 +23,7 @@ import pytest
 import oracle
 import synth
 import paper_1809_07014_gb300 as pkg
-from tests.helpers import decode_keys
+from tests.helpers import assert_same, decode_keys, fnv1a_keys
 
 pytestmark = pytest.mark.gpu
 K = 31
@@ -42,19 +46,6 @@ def revcomp_packed(x: np.ndarray) -> np.ndarray:
     out = np.zeros_like(y)
     for j in range(K):  # base j (from the right) goes to position K-1-j
         out |= ((y >> np.uint64(2 * j)) & np.uint64(3)) << np.uint64(2 * (K - 1 - j))
-    return out
-
-
-def classify_rule(ext4: np.ndarray, count: np.ndarray, p) -> np.ndarray:
-    """Depth-adaptive rule written over arrays (property check at full size)."""
-    best = ext4.max(1)
-    m = ext4.argmax(1)
-    ties = (ext4 == best[:, None]).sum(1)
-    alt = ext4.sum(1) - best
-    lim = np.maximum(np.uint64(p.t_base * p.err_den), np.uint64(p.err_num) * count)
-    out = np.where(alt * np.uint64(p.err_den) <= lim, m, 4).astype(np.uint8)
-    out[ties > 1] = 4
-    out[best == 0] = 5
     return out
 
 
@@ -84,9 +75,29 @@ def valid_windows(rs) -> int:
     return total - lost
 
 
-def test_metagenome_2gbases_k31(tmp_path):
+N_SHARDS = 64
+SHARDS = (0, 4)  # keys with FNV-1a(key) mod 64 in [0, 4)
+
+
+def fnv1a_shard_packed(keys: np.ndarray, k: int) -> np.ndarray:
+    """FNV-1a 64 of the k-letter string of each packed one-word key, computed
+    on the GPU with torch (test-side selection of the GPU survivors in a
+    shard); 64-bit products wrap, so the low bits are exact."""
     import torch
-    threads = os.cpu_count() or 1
+    x = torch.from_numpy(keys.view(np.int64)).cuda()
+    lut = torch.tensor([ord("A"), ord("C"), ord("G"), ord("T")], dtype=torch.int64, device="cuda")
+    h = torch.full_like(x, 14695981039346656037 - (1 << 64))
+    prime = 1099511628211
+    for j in range(k):
+        code = (x >> (2 * (k - 1 - j))) & 3
+        h = (h ^ lut[code]) * prime
+    return h.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module")
+def fullsize():
+    import torch
+    threads = oracle.host_threads()
     rs = synth.generate(synth.METAGENOME_2G, threads=threads)
     dev = [torch.from_numpy(a).cuda() for a in (rs.bases, rs.quals, rs.offsets.view(np.int64))]
     stream = torch.cuda.current_stream()
@@ -98,6 +109,30 @@ def test_metagenome_2gbases_k31(tmp_path):
     ka.close()
     r.close()
     del dev
+    torch.cuda.empty_cache()
+    return rs, res, st
+
+
+def test_metagenome_2gbases_k31_complete_on_hash_shards(fullsize):
+    rs, res, _ = fullsize
+    p = oracle.Params(k=K)
+    h = fnv1a_shard_packed(res.keys[:, 0], K)
+    # the torch hash agrees with the plain vectorised FNV-1a of the decoded strings
+    probe = np.random.default_rng(7).choice(len(res), 2000, replace=False)
+    assert (h[probe] == fnv1a_keys(decode_keys(res.keys[probe], K))).all()
+    sh = h % np.uint64(N_SHARDS)
+    sel = np.nonzero((sh >= SHARDS[0]) & (sh < SHARDS[1]))[0]
+    want = oracle.run_threads(rs.bases, rs.quals, rs.offsets, p, SHARDS[0], SHARDS[1], N_SHARDS,
+                              threads=oracle.host_threads())
+    assert len(want) > 1_000_000
+    part = pkg.Result(keys=res.keys[sel], count=res.count[sel], ext=res.ext[sel], cls=res.cls[sel], k=K,
+                      windows=want.windows, distinct=want.distinct)
+    assert_same(part, want, f"2-Gbase k=31, shards {SHARDS[0]}-{SHARDS[1] - 1} of {N_SHARDS}")
+
+
+def test_metagenome_2gbases_k31(fullsize):
+    rs, res, st = fullsize
+    threads = oracle.host_threads()
     p = oracle.Params(k=K)
     n = len(res)
     assert st["retries"] == 0 or st["retries"] <= 2
@@ -114,8 +149,6 @@ def test_metagenome_2gbases_k31(tmp_path):
     ext = res.ext.astype(np.uint64)
     assert (cnt >= p.min_count).all()
     assert (ext[:, :4].sum(1) <= cnt).all() and (ext[:, 4:].sum(1) <= cnt).all()
-    assert (classify_rule(ext[:, :4], cnt, p) == res.cls[:, 0]).all()
-    assert (classify_rule(ext[:, 4:], cnt, p) == res.cls[:, 1]).all()
     # ---- sampled exact comparison with the oracle over all reads
     rng = np.random.default_rng(2026)
     pick = rng.choice(n, 3000, replace=False)

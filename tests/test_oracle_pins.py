@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from tests import helpers
 
 COMP = {"A": "T", "C": "G", "G": "C", "T": "A"}
 ORDER = "ACGT"
@@ -365,3 +366,42 @@ def test_count_keys_matches_full_definition():
         if absent[0] not in set(full.keys):
             c, e, cl = oracle.count_keys(rs.bases, rs.quals, rs.offsets, p, absent, threads=2)
             assert c[0] == 0 and (e == 0).all() and tuple(cl[0]) == (oracle.DEAD_END, oracle.DEAD_END)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_threaded_sharded_mode_against_brute_force(seed):
+    """The threaded form (reads split over threads, partial maps summed before
+    the filter) restricted to a shard range equals the brute-force scan
+    restricted to the keys whose FNV-1a hash falls in that range."""
+    rng = random.Random(1000 + seed)
+    reads = random_reads(rng, rng.randint(1, 30), 1, 40, alphabet=rng.choice(["ACGT", "AC"]),
+                         n_rate=rng.choice([0.0, 0.03]))
+    k = rng.choice([1, 3, 5, 7, 11])
+    p = oracle.Params(k=k, min_count=rng.choice([1, 2, 3]), qual_threshold=rng.choice([0, 20, 30]),
+                      ext_mode=rng.choice([0, 1]))
+    bases = b"".join(r[0] for r in reads)
+    quals = b"".join(r[1] for r in reads)
+    offsets = np.zeros(len(reads) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([len(r[0]) for r in reads], dtype=np.uint64)
+    full, _, _ = brute_force(reads, p)
+    n_shards = rng.choice([1, 2, 5])
+    lo = rng.randrange(n_shards)
+    hi = rng.randrange(lo + 1, n_shards + 1)
+    want = [row for row in full if lo <= helpers.fnv1a_keys(np.array([row[0]], dtype=f"S{k}"))[0] % n_shards < hi]
+    for threads in (1, 2, 3, 7):
+        got = oracle.run_threads(bases, quals, offsets, p, lo, hi, n_shards, threads)
+        assert as_rows(got) == want, (threads, lo, hi, n_shards)
+
+
+def test_threaded_mode_equals_single_thread_on_a_metagenome_slice():
+    rs = synth.generate(synth.METAGENOME_2G.scaled(3000))
+    p = oracle.Params(k=31)
+    one = oracle.run(rs.bases, rs.quals, rs.offsets, p)
+    many = oracle.run_threads(rs.bases, rs.quals, rs.offsets, p, threads=5)
+    assert as_rows(many) == as_rows(one)
+    assert (many.windows, many.distinct) == (one.windows, one.distinct)
+    parts = [oracle.run_threads(rs.bases, rs.quals, rs.offsets, p, lo, lo + 3, 9, threads=4) for lo in (0, 3, 6)]
+    assert sum(x.windows for x in parts) == one.windows
+    assert sum(x.distinct for x in parts) == one.distinct
+    merged = sorted(r for x in parts for r in as_rows(x))
+    assert merged == as_rows(one)

@@ -1,14 +1,16 @@
 """Serving: requests that arrive while others run are admitted as memory
 frees up and overlap on the device; every result is the same alone and in
-the mix (exact: all integer)."""
+the mix, and equal to the oracle's (exact: all integer)."""
 import threading
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 import paper_1809_07014_gb300 as pkg
+from tests.helpers import assert_same
 from tests.test_batch_gpu import same_result
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +24,9 @@ def readsets():
     for i, n in enumerate([40000, 3000, 15000, 800, 25000, 6000]):
         s = synth.generate(synth.metagenome_sample(20 + i, n * 150, n_genomes=4 + i).scaled(
             n, genome_len_min=30_000, genome_len_max=90_000))
-        out.append(pkg.ReadSet(s.bases, s.quals, s.offsets))
+        r = pkg.ReadSet(s.bases, s.quals, s.offsets)
+        r.src = s  # the reads themselves, for the oracle
+        out.append(r)
     return out
 
 
@@ -64,6 +68,41 @@ def test_results_same_alone_and_in_the_mix(readsets):
     assert st["completed"] == len(REQUESTS) and st["failed"] == 0
     assert st["peak_running"] >= 2, "requests never overlapped"
     srv.close()
+
+
+ORACLE_REQUESTS = [(1, 33), (3, 77), (5, 99), (2, 55), (0, 21), (5, 21), (3, 99), (1, 77), (4, 33), (2, 21)]
+
+
+def test_served_results_equal_the_oracle(readsets):
+    """Staggered requests from three client threads, mixed k (one to four
+    words per key), four workers: every served result equals the oracle on
+    that request's reads, element by element."""
+    srv = pkg.Server(workers=4)
+    ids = {}
+
+    def client(part):
+        for i in part:
+            r, k = ORACLE_REQUESTS[i]
+            ids[i] = srv.submit(readsets[r], k)
+            time.sleep(0.003 * (1 + i % 4))
+
+    threads = [threading.Thread(target=client, args=(list(range(j, len(ORACLE_REQUESTS), 3)),)) for j in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    got = {}
+    for i, rid in ids.items():
+        got[i] = srv.results(rid)
+        srv.release(rid)
+    st = srv.stats()
+    assert st["completed"] == len(ORACLE_REQUESTS) and st["failed"] == 0
+    assert st["peak_running"] >= 2, "requests never overlapped"
+    srv.close()
+    for i, (r, k) in enumerate(ORACLE_REQUESTS):
+        s = readsets[r].src
+        want = oracle.run_threads(s.bases, s.quals, s.offsets, oracle.Params(k=k), threads=oracle.host_threads())
+        assert_same(got[i], want, f"served request {i} (readset {r}, k={k})")
 
 
 def test_admission_by_footprint_queues_and_stays_exact(readsets):
