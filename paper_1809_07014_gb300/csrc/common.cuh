@@ -12,8 +12,8 @@
 //                  "tail") holds the low bits of z, a bijective mix of the
 //                  key's last word, with the partition bits of z removed
 //                  (they are implied by the partition the record sits in),
-//                  shifted left by 6, and the window's extension code e5 in
-//                  the low 5 bits.
+//                  shifted left by 6, and the window's extension code in
+//                  the low 6 bits (left code << 3 | right code).
 //
 // The partitioning is the device-wide form of the paper's owner-computes
 // k-mer histogram (Sec. II-A, use case 4; Sec. II-B): a hash of the k-mer
@@ -46,12 +46,11 @@ enum StatusBits : unsigned int {
     ST_L2_PLAN = 1u << 7,        // the level-2 planner found the leaf layout larger than the buffer
 };
 
-// Extension code of one window: left and right in {0 = none, 1..4 = A,C,G,T + 1}.
-__host__ __device__ inline unsigned ext_code(unsigned left, unsigned right) { return left * 5u + right; }
-
-// Record tail bit that marks an occupied table key (e5 < 25 never sets it).
-constexpr unsigned long long kKeyMark = 32ull;
-constexpr unsigned long long kBusy = 1ull;
+// Extension code of one window: left and right in {0 = none, 1..4 = A,C,G,T + 1},
+// three bits each.
+__host__ __device__ inline unsigned ext_code(unsigned left, unsigned right) { return (left << 3) | right; }
+__host__ __device__ inline unsigned ext_left(unsigned long long tail) { return (unsigned)(tail >> 3) & 7u; }
+__host__ __device__ inline unsigned ext_right(unsigned long long tail) { return (unsigned)tail & 7u; }
 
 // ---------------------------------------------------------------- mixing
 __host__ __device__ constexpr unsigned long long inv_odd(unsigned long long c) {
@@ -155,7 +154,8 @@ struct Job {
     unsigned table_ratio_num;
     // status and statistics
     unsigned int* status;
-    unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted, [3] leaves split
+    unsigned long long* stats;  // [0] windows counted, [1] distinct keys, [2] records emitted,
+                                // [3] leaves counted in rounds, [4] heavy sub-bins walked in key ranges
 };
 
 // ------------------------------------------------------------ classify

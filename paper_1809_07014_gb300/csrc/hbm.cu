@@ -147,9 +147,7 @@ __global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const 
         for (int w = 0; w < W - 1; ++w) key[w] = recs[(start + i) * W + w];
         const unsigned long long z = record_z(g, j.pass, bucket, tail);
         key[W - 1] = z_to_tail<W>(z, key, g.bt);
-        const unsigned e5 = (unsigned)(tail & 31ull);
-        const unsigned l = e5 / 5u, r = e5 - 5u * l;
-        if (!hbm_insert<W>(t, cap, key, z, l, r, j.status)) break;
+        if (!hbm_insert<W>(t, cap, key, z, ext_left(tail), ext_right(tail), j.status)) break;
         ++windows;
     }
 #pragma unroll

@@ -35,6 +35,10 @@ constexpr unsigned kSpinLimit = 1u << 22;
 constexpr unsigned kMaxGroupProbes = 16;  // 64 slots; a longer chain sends the leaf to the fallback
 constexpr unsigned kLanePlanes = 5;
 constexpr unsigned kMaxSubBits = 4;       // a leaf is split into at most 16 key ranges
+// Slot tail of an occupied key: the record tail with its extension bits
+// replaced by this mark; bit 0 marks a slot being published (W > 2).
+constexpr unsigned long long kKeyMark = 32ull;
+constexpr unsigned long long kBusy = 1ull;
 
 template <int W>
 struct LeafShape {
@@ -198,7 +202,6 @@ template <int W>
 __device__ __forceinline__ void insert_record(const Table& t, const unsigned long long (&rec)[W], unsigned ngroups,
                                               unsigned* s_flags) {
     const unsigned long long tail = rec[W - 1];
-    const unsigned e5 = (unsigned)(tail & 31ull);
     const unsigned long long ktail = (tail & ~63ull) | kKeyMark;
     // home group from every in-leaf bit of z (for short keys the top bits of the
     // low word are partition bits, constant within a leaf): multiplicative hash
@@ -254,7 +257,7 @@ __device__ __forceinline__ void insert_record(const Table& t, const unsigned lon
         atomicOr(s_flags, kLeafFull);
         return;
     }
-    const unsigned l = e5 / 5u, r = e5 - 5u * l;
+    const unsigned l = ext_left(tail), r = ext_right(tail);
     bump(t, (unsigned)found, l ? l - 1 : 4u);  // every window has exactly one left lane
     if (r) bump(t, (unsigned)found, 4u + r);
 }
