@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--reads", type=int, default=0, help="override the number of reads (development only)")
     ap.add_argument("--variant", choices=["partitioned", "hbm_table"], default="partitioned")
     ap.add_argument("--leaf-bits", type=int, default=0)
-    ap.add_argument("--mode", choices=["single", "batched", "serve", "multik"], default="single",
+    ap.add_argument("--mode", choices=["single", "batched", "serve", "multik", "large"], default="single",
                     help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
                          "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
     ap.add_argument("--scale", type=float, default=1.0, help="batched/serve: scale every sample size")
@@ -709,6 +709,95 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- large instance
+LARGE_BUDGET = 180 * 10**9
+
+
+def large_recipe():
+    import synth
+    return synth.Recipe("metagenome-500-genomes-15Gbases", seed=55, n_genomes=500, genome_len_min=1_000_000,
+                        genome_len_max=5_000_000, abundance_sigma=1.5, n_reads=100_000_000, subst_rate=0.01,
+                        err_qual_lo=2, err_qual_hi=12, n_rate=1e-4)
+
+
+def run_large(args):
+    """The 15-Gbase, 500-genome instance at k = 55 within 180 GB of device
+    memory (readset included): with the Bloom gate (k-mers seen once kept out
+    of the counting pass) and without it, each after one warm-up query.  The
+    survivors go straight to page-locked host arrays as the leaves find them
+    (kmer_analysis_query_into with KMER_HOST), so that the device memory holds
+    the reads, the records and the filters only."""
+    import torch
+
+    import synth
+    import paper_1809_07014_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    r = large_recipe()
+    if args.scale != 1.0:
+        r = r.scaled(max(1, int(r.n_reads * args.scale)))
+    t0 = time.perf_counter()
+    s = synth.generate(r)
+    rs = pkg.ReadSet(s.bases, s.quals, s.offsets, stream=stream)
+    n_bases = s.n_bases
+    del s
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    # the packed readset counts against the 180 GB: 16 bytes per 32-base block,
+    # and the base and block offsets (8 bytes each per read)
+    n_reads = r.n_reads
+    rs_bytes = 16 * (n_bases // 32 + n_reads) + 16 * (n_reads + 1)
+    budget = LARGE_BUDGET - rs_bytes
+    cap = int(0.06 * n_bases) + 4096  # survivors: about 0.81 G at this size
+    t0 = time.perf_counter()
+    keys = torch.empty((cap, 2), dtype=torch.int64).pin_memory()
+    cnt = torch.empty(cap, dtype=torch.int32).pin_memory()
+    ext = torch.empty((cap, 8), dtype=torch.int32).pin_memory()
+    cls = torch.empty((cap, 2), dtype=torch.uint8).pin_memory()
+    pin_s = time.perf_counter() - t0
+    out = {}
+    for name, flags in (("gated", pkg.KMER_FLAG_BLOOM_GATE), ("ungated", 0)):
+        ka = pkg.KmerAnalysis(55, stream=stream, memory_budget=budget, flags=flags | pkg.KMER_FLAG_PROFILE)
+        runs = []
+        for i in range(2):
+            ka.reset()
+            ka.submit(rs)
+            torch.cuda.synchronize()
+            free_b, total_b = torch.cuda.mem_get_info()
+            print(f"large: {name} query {i}: device free {free_b / 1e9:.1f} of {total_b / 1e9:.1f} GB",
+                  file=sys.stderr, flush=True)
+            t1 = time.perf_counter()
+            v = pkg.kmer_analysis_query_into(ka.handle, keys.data_ptr(), cnt.data_ptr(), ext.data_ptr(),
+                                             cls.data_ptr(), cap, pkg.KMER_HOST)
+            torch.cuda.synchronize()
+            runs.append(time.perf_counter() - t1)
+            st = ka.stats()
+            print(f"large: {name} query {i}: {runs[-1]:.3f} s, passes {st['passes']}, waves {st['l2_waves']}, "
+                  f"records {st['records_emitted']}, device bytes {st['device_bytes']}, gate first {st['gate_first']} "
+                  f"twice {st['gate_twice']}", file=sys.stderr, flush=True)
+        out[name] = {"s": round(runs[-1], 4), "first_query_s": round(runs[0], 4),
+                     "k-mers/s": int(v.windows) / runs[-1], "windows": int(v.windows),
+                     "distinct": int(v.distinct), "survivors": int(v.n), "passes": st["passes"],
+                     "l2_waves": st["l2_waves"], "records_emitted": st["records_emitted"],
+                     "device_bytes_analysis": st["device_bytes"],
+                     "gate_first": st["gate_first"], "gate_twice": st["gate_twice"],
+                     "stages_ms": {k: round(st[k], 2) for k in ("ms_gate", "ms_scatter", "ms_repart", "ms_leaf",
+                                                                 "ms_fallback")}}
+        ka.close()
+    line = {"metric": METRIC, "value": out["gated"]["k-mers/s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * out["gated"]["s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"one instance: {n_bases / 1e9:.1f} Gbases of 150 bp reads from 500 genomes "
+                                   f"(log-normal abundance, 1% substitutions), k=55",
+                       "budget_bytes": LARGE_BUDGET, "readset_bytes": int(rs_bytes),
+                       "analysis_budget_bytes": int(budget)},
+            "gated": out["gated"], "ungated": out["ungated"], "setup_s": round(gen_s, 1),
+            "pinned_output_bytes": int(cap * (16 + 4 + 32 + 2)), "pin_s": round(pin_s, 1)}
+    print(json.dumps(line), flush=True)
+    rs.close()
+
+
 # ------------------------------------------------------------- multi-k
 def run_multik(args):
     """The single-genome reads (20 000 x 150 bp) resident on the device, analysed
@@ -768,6 +857,8 @@ def main():
         run_serve(args)
     elif args.mode == "multik":
         run_multik(args)
+    elif args.mode == "large":
+        run_large(args)
     else:
         run_ours(args)
 

@@ -117,6 +117,20 @@ typedef struct {
 /* flags: record CUDA events around each stage on the analysis stream and
  * report the per-stage device times in kmer_analysis_stats. */
 #define KMER_FLAG_PROFILE 1u
+/* flags: Bloom-filter gate (Sec. II-B: Bloom filters keep erroneous k-mers,
+ * mostly seen once, out of the hash tables).  A first pass over the reads
+ * adds every window's canonical k-mer to a blocked Bloom filter F1 and
+ * k-mers already in F1 to a second filter F2; the counting pass then keeps
+ * only the windows of k-mers in F2.  Exact for min_count >= 2 (a k-mer seen
+ * twice is always in F2; a k-mer seen once that slips through as a false
+ * positive is counted, once, and dropped): keys, counts, tallies, classes
+ * and `windows` are those of the ungated analysis, while `distinct` counts
+ * only the k-mers that passed the gate.  Costs two filters of 8 bits per
+ * expected distinct k-mer (about one byte per window on a first query) and
+ * one more pass over the reads; pays where k-mers seen once are a large
+ * share of the windows and memory is tight.  Requires min_count >= 2 and the
+ * partitioned variant (INVALID_ARG otherwise); ignored by batches. */
+#define KMER_FLAG_BLOOM_GATE 2u
 
 /* Results of the last query.  Device pointers owned by the analysis; valid
  * until the next submit, query, reset or destroy of the same handle. */
@@ -151,6 +165,15 @@ typedef struct {
     uint32_t n_scatter, n_repart, n_leaf, n_fallback;
     uint64_t records_l2;        /* records moved by the level-2 repartition */
     uint64_t leaf_splits;       /* partitions whose keys did not fit one table and were counted in key ranges */
+    uint64_t l2_waves;          /* level-2 waves (windows of level-1 buckets repartitioned and counted one after
+                                   another, when their records do not fit the memory budget together); 0 = the
+                                   level-2 stages took every bucket at once */
+    uint64_t gate_first;        /* KMER_FLAG_BLOOM_GATE: windows whose k-mer the gate saw first (about the
+                                   distinct k-mers) */
+    uint64_t gate_twice;        /* KMER_FLAG_BLOOM_GATE: k-mers the gate saw at least twice (about the k-mers
+                                   the counting pass kept) */
+    float ms_gate;              /* with KMER_FLAG_PROFILE: device time of the gate's pass */
+    uint32_t n_gate;
 } kmer_analysis_stats;
 
 /* Fills *p with defaults: min_count 2, qual_offset 33, qual_threshold 20,

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -107,7 +108,7 @@ void pinned_misc_put(Misc* m) {
 }
 
 Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
-                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits) {
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves) {
     Geometry g{};
     g.k = k;
     g.W = (2 * k + 63) / 64;
@@ -122,13 +123,15 @@ Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long lon
     const unsigned need = g.bt > 58 ? g.bt - 58 : 0;  // partition bits implied by the record format
     p = std::max(p, need);
     p = std::min(p, g.bt);
-    // passes: records of one pass (two levels, with slack) must fit the budget
+    // passes: records of one pass (two levels, with slack) must fit the budget;
+    // with level-2 waves, the level-1 records and one wave of the level 2
     const double rec_bytes = 8.0 * g.W;
     unsigned ps = 0;
     for (;;) {
         const double win = (double)windows / (double)(1ull << ps);
-        const double bytes = win * rec_bytes * 3.5 + 64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
-        if (bytes <= 0.8 * (double)budget || ps >= p || ps >= 12) break;
+        const double bytes = win * rec_bytes * (waves ? 1.02 + 2.1 / kMaxWaves : 3.5) +
+                             64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
+        if (bytes <= (waves ? 0.9 : 0.8) * (double)budget || ps >= p || ps >= 12) break;
         ++ps;
     }
     const unsigned lb = p - ps;
@@ -167,6 +170,7 @@ struct kmer_analysis {
     DevBuf l2_rec, l2_base, l2_leafcap, l2_fill, l2_leaf_start, tile_prefix;
     DevBuf out_keys, out_count, out_ext, out_cls;
     DevBuf fb_list, split_list, hbm, misc;
+    DevBuf gate1, gate2, gate_cnt;  // Bloom gate: filters F1, F2 and the gate pass's counters
     DevBuf lk_index, lk_keys, lk_out;  // survivors' index for lookups, staging of host lookups
     // survivors written straight into caller buffers (kmer_analysis_query_into): device
     // addresses of those buffers while such a query runs, and of the results after it
@@ -180,7 +184,7 @@ struct kmer_analysis {
     unsigned long long out_cap = 0, fb_cap = 0;
     Misc* host_misc = nullptr;  // pinned
     // profiling (KMER_FLAG_PROFILE): one begin/end event pair per stage
-    enum { STG_SCATTER, STG_REPART, STG_LEAF, STG_FALLBACK, STG_N };
+    enum { STG_SCATTER, STG_REPART, STG_LEAF, STG_FALLBACK, STG_GATE, STG_N };
     cudaEvent_t ev_b[STG_N] = {}, ev_e[STG_N] = {};
     bool ev_pending[STG_N] = {};
     // results
@@ -193,6 +197,9 @@ struct kmer_analysis {
     double hist_ratio = 0.0;
     unsigned l2_slack_num = 512;  // leaf capacity = 2 * mean + 256
     double hint_ratio = 0.0;      // distinct_hint / windows of the current query (0 = no hint)
+    // Bloom gate: filter words (log2), and first sightings / windows at hist_k
+    unsigned gate_bits = 0;
+    double gate_ratio = 0.0;
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -201,7 +208,7 @@ struct kmer_analysis {
                               &l2_leaf_start, &tile_prefix, &out_keys, &out_count, &out_ext, &out_cls,
                               &fb_list, &split_list, &hbm, &misc, &lk_index, &lk_keys, &lk_out, &d_ajob,
                               &d_sjobs, &d_tile_off, &d_leaf_off,
-                              &d_job_tile_off};
+                              &d_job_tile_off, &gate1, &gate2, &gate_cnt};
         size_t t = 0;
         for (auto* b : bs) t += b->bytes;
         return t;
@@ -222,7 +229,12 @@ int validate_params(const kmer_analysis_params* p) {
         return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
     if (p->leaf_bits > 22) return fail(KMER_ERR_INVALID_ARG, "leaf_bits must be <= 22");
     if (p->l1_bits > 11) return fail(KMER_ERR_INVALID_ARG, "l1_bits must be <= 11");
-    if (p->flags & ~KMER_FLAG_PROFILE) return fail(KMER_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
+    if (p->flags & ~(KMER_FLAG_PROFILE | KMER_FLAG_BLOOM_GATE))
+        return fail(KMER_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
+    if ((p->flags & KMER_FLAG_BLOOM_GATE) && p->min_count < 2)
+        return fail(KMER_ERR_INVALID_ARG, "the Bloom gate needs min_count >= 2 (it drops k-mers seen once)");
+    if ((p->flags & KMER_FLAG_BLOOM_GATE) && p->variant != KMER_VARIANT_PARTITIONED)
+        return fail(KMER_ERR_INVALID_ARG, "the Bloom gate works with the partitioned variant only");
     for (unsigned r : p->reserved)
         if (r) return fail(KMER_ERR_INVALID_ARG, "reserved fields must be zero");
     return KMER_OK;
@@ -392,17 +404,21 @@ struct Plan {
     Geometry g;
     unsigned passes;
     unsigned long long windows;  // upper bound (N windows included)
+    size_t budget;               // device bytes for the records of a pass
 };
 
-Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget, unsigned cap_max) {
+Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget, unsigned cap_max,
+               unsigned long long gated_distinct = 0) {
     Plan pl{};
     pl.windows = windows;
     unsigned long long basis = windows;
-    if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
+    if (gated_distinct) basis = std::min<unsigned long long>(windows, gated_distinct + gated_distinct / 8 + 1024);
+    else if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
     else if (h->hist_k == h->p.k && h->hist_ratio > 0.0)  // learned from the previous query at this k
         basis = std::min<unsigned long long>(windows, (unsigned long long)(1.15 * h->hist_ratio * (double)windows) + 1);
-    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, h->p.l1_bits);
+    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, h->p.l1_bits, true);
     pl.passes = 1u << pl.g.ps;
+    pl.budget = budget;
     return pl;
 }
 
@@ -534,8 +550,8 @@ int prof_end(kmer_analysis* h, int stg) {
 // After the stream was synchronised: add the elapsed time of finished stages.
 int prof_collect(kmer_analysis* h) {
     if (!profiling(h)) return KMER_OK;
-    float* dst[] = {&h->st.ms_scatter, &h->st.ms_repart, &h->st.ms_leaf, &h->st.ms_fallback};
-    uint32_t* cnt[] = {&h->st.n_scatter, &h->st.n_repart, &h->st.n_leaf, &h->st.n_fallback};
+    float* dst[] = {&h->st.ms_scatter, &h->st.ms_repart, &h->st.ms_leaf, &h->st.ms_fallback, &h->st.ms_gate};
+    uint32_t* cnt[] = {&h->st.n_scatter, &h->st.n_repart, &h->st.n_leaf, &h->st.n_fallback, &h->st.n_gate};
     for (int i = 0; i < kmer_analysis::STG_N; ++i) {
         if (!h->ev_pending[i]) continue;
         float ms = 0.f;
@@ -547,15 +563,16 @@ int prof_collect(kmer_analysis* h) {
     return KMER_OK;
 }
 
-// HBM-table recount of the leaves listed by the leaf kernel.
+// HBM-table recount of the leaves listed by the leaf kernel (leaves of the
+// job's bucket window).
 int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     if (n_fb == 0) return KMER_OK;
-    const unsigned P = 1u << (j.g.p1 + j.g.p2);
+    const unsigned P = j.g.p2 ? job_buckets(j) << j.g.p2 : job_buckets(j);
     std::vector<unsigned> leaves(n_fb);
     CK(cudaMemcpyAsync(leaves.data(), h->fb_list.p, n_fb * 4ull, cudaMemcpyDeviceToHost, h->stream));
-    std::vector<unsigned long long> fill(j.g.p2 ? P : (1u << j.g.p1));
-    CK(cudaMemcpyAsync(fill.data(), j.g.p2 ? h->l2_fill.p : h->l1_fill.p, fill.size() * 8, cudaMemcpyDeviceToHost,
-                       h->stream));
+    std::vector<unsigned long long> fill(P);
+    CK(cudaMemcpyAsync(fill.data(), j.g.p2 ? (const void*)j.l2_fill : (const void*)j.l1_fill, fill.size() * 8,
+                       cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     unsigned long long extra_out = 0, max_n = 0;
     for (unsigned e : leaves) {  // a range's records are at most its leaf's
@@ -583,19 +600,132 @@ int run_fallbacks(kmer_analysis* h, Job& j, unsigned n_fb) {
     return status_error(h->host_misc->status);
 }
 
-// One pass of the partitioned variant over every submitted readset.
+// Totals of the level-2 waves of one pass.
+struct WaveTotals {
+    unsigned long long out_n = 0, windows = 0, distinct = 0, splits = 0, emitted = 0;
+};
+
+// Level-2 stages (repartition, leaves, fallbacks) of one pass over the
+// level-1 buckets [b0, b0 + nb) (a wave, or all of them), with their retries.
+// `fresh`: reset the device counters first (keeping out_n and the scatter's
+// emitted count).  Sets *rescatter when a level-1 bucket overflowed.
+int run_level2(kmer_analysis* h, Job j, unsigned b0, unsigned nb, unsigned long long l2_capacity, unsigned cap_max,
+               bool fresh, WaveTotals& tot, bool* rescatter) {
+    const Geometry g = j.g;
+    const unsigned P1 = 1u << g.p1, P2 = 1u << g.p2, W = g.W;
+    const unsigned Pw = g.p2 ? nb << g.p2 : nb;  // leaves of the wave
+    j.bucket0 = b0;
+    j.n_buckets = (b0 == 0 && nb == P1) ? 0 : nb;
+    j.l1_start += b0;
+    j.l1_cap += b0;
+    j.l1_fill += b0;
+    std::vector<unsigned long long> exact_leaf;  // exact level-2 layout after an overflow
+    if (g.p2) {
+        TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
+        TRY(h->l2_base.ensure(nb * 8ull));
+        TRY(h->l2_leafcap.ensure(nb * 4ull));
+        TRY(h->l2_fill.ensure(Pw * 8ull));
+        TRY(h->tile_prefix.ensure((nb + 1) * 8ull));
+        j.l2_rec = h->l2_rec.as<unsigned long long>();
+        j.l2_base = h->l2_base.as<unsigned long long>();
+        j.l2_leafcap = h->l2_leafcap.as<unsigned int>();
+        j.l2_fill = h->l2_fill.as<unsigned long long>();
+        j.tile_prefix = h->tile_prefix.as<unsigned long long>();
+        j.l2_leaf_start = nullptr;
+    }
+    TRY(h->split_list.ensure((size_t)Pw * 4));  // every leaf could need key ranges
+    fill_job_outputs(h, j);
+    if (fresh) TRY(reset_misc(h, tot.out_n, tot.emitted));
+    const std::vector<unsigned long long> leaf_off = {0ull, (unsigned long long)Pw};
+    TRY(upload(h, h->d_leaf_off, leaf_off));
+    TRY(h->d_job_tile_off.ensure(2 * 8));
+    for (unsigned sub_attempt = 0;; ++sub_attempt) {
+        if (sub_attempt > 8) return fail(KMER_ERR_TABLE_FULL, "leaf buffers still too small after retries");
+        j.l2_capacity = exact_leaf.empty() ? l2_capacity : ~0ull;
+        TRY(upload(h, h->d_ajob, std::vector<Job>{j}));
+        if (g.p2) {
+            CK(cudaMemsetAsync(h->l2_fill.p, 0, Pw * 8ull, h->stream));
+            TRY(prof_begin(h, kmer_analysis::STG_REPART));
+            CK(launch_l2_plan(h->d_ajob.as<Job>(), 1, h->d_job_tile_off.as<unsigned long long>(), h->stream));
+            CK(launch_repart(W, h->d_ajob.as<Job>(), h->d_job_tile_off.as<unsigned long long>(), 1, g.p2,
+                             h->num_sms, h->stream));
+            TRY(prof_end(h, kmer_analysis::STG_REPART));
+            h->st.launches += 3;
+        }
+        TRY(prof_begin(h, kmer_analysis::STG_LEAF));
+        CK(launch_leaf(W, h->d_ajob.as<Job>(), h->d_leaf_off.as<unsigned long long>(), 1, Pw, cap_max, h->num_sms,
+                       h->stream));
+        CK(launch_leaf_split(W, h->d_ajob.as<Job>(), 1, cap_max, h->num_sms, h->stream));
+        TRY(prof_end(h, kmer_analysis::STG_LEAF));
+        h->st.launches += 2;
+        TRY(read_misc(h));
+        TRY(prof_collect(h));
+        const Misc m = *h->host_misc;
+        tot.emitted = m.stats[2];
+        if (m.status & ST_L1_OVERFLOW) {  // re-scatter with exact bucket sizes
+            *rescatter = true;
+            return KMER_OK;
+        }
+        if (m.status & ST_L2_OVERFLOW) {
+            std::vector<unsigned long long> fill(Pw);
+            CK(cudaMemcpyAsync(fill.data(), h->l2_fill.p, Pw * 8ull, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            h->l2_slack_num = std::min(4096u, h->l2_slack_num * 3 / 2);  // future queries: more slack
+            exact_leaf.assign(Pw + 1, 0);
+            for (unsigned i = 0; i < Pw; ++i) exact_leaf[i + 1] = exact_leaf[i] + fill[i];
+            l2_capacity = exact_leaf[Pw];
+            TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
+            TRY(h->l2_leaf_start.ensure((Pw + 1) * 8ull));
+            CK(cudaMemcpyAsync(h->l2_leaf_start.p, exact_leaf.data(), (Pw + 1) * 8ull, cudaMemcpyHostToDevice,
+                               h->stream));
+            j.l2_rec = h->l2_rec.as<unsigned long long>();
+            j.l2_leaf_start = h->l2_leaf_start.as<unsigned long long>();
+            h->st.retries++;
+            TRY(reset_misc(h, tot.out_n, m.stats[2]));
+            continue;
+        }
+        if (m.status & (ST_OUT_OVERFLOW | ST_FALLBACK_FULL)) {
+            if (m.status & ST_OUT_OVERFLOW) TRY(ensure_output(h, m.out_n + m.out_n / 16 + 1024, tot.out_n));
+            if (m.status & ST_FALLBACK_FULL) {
+                TRY(h->fb_list.ensure((m.fb_n + 64) * 4ull));
+                h->fb_cap = m.fb_n + 64;
+            }
+            fill_job_outputs(h, j);
+            h->st.retries++;
+            TRY(reset_misc(h, tot.out_n, m.stats[2]));
+            continue;
+        }
+        TRY(status_error(m.status));
+        h->st.fallback_leaves += m.fb_n;
+        TRY(run_fallbacks(h, j, m.fb_n));
+        const Misc fin = *h->host_misc;
+        if (fin.status & ST_OUT_OVERFLOW) return fail(KMER_ERR_CUDA, "fallback output overflow");
+        tot.out_n = fin.out_n;
+        tot.windows += fin.stats[0];
+        tot.distinct += fin.stats[1];
+        tot.splits += fin.stats[3];
+        return KMER_OK;
+    }
+}
+
+// One pass of the partitioned variant over every submitted readset: the
+// scatter, then the level-2 stages over all level-1 buckets at once, or in
+// waves of buckets when their level-2 records do not fit the budget together.
 int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) {
     Geometry g = pl.g;
-    const unsigned P1 = 1u << g.p1, P = 1u << (g.p1 + g.p2);
+    const unsigned P1 = 1u << g.p1, P2 = 1u << g.p2;
     const unsigned W = g.W;
     const unsigned long long pass_windows = (pl.windows + pl.passes - 1) / pl.passes;
     std::vector<unsigned long long> caps(P1), starts(P1 + 1);
     {
+        // the mixed key spreads records evenly: four standard deviations of
+        // slack (a bucket that still overflows is re-scattered with exact sizes)
         const unsigned long long mean = (pass_windows + P1 - 1) / P1;
-        for (unsigned b = 0; b < P1; ++b) caps[b] = mean + mean / 8 + 1024;
+        const unsigned long long slack = 4 * (unsigned long long)std::sqrt((double)mean) + 1024;
+        for (unsigned b = 0; b < P1; ++b) caps[b] = mean + slack;
     }
-    std::vector<unsigned long long> exact_leaf;  // exact level-2 layout after an overflow
     const unsigned long long out_start = h->n_out;
+    const double slack = (double)h->l2_slack_num / 256.0;
     for (unsigned attempt = 0;; ++attempt) {
         if (attempt > 8) return fail(KMER_ERR_TABLE_FULL, "buffers still too small after %u retries", attempt);
         starts[0] = 0;
@@ -611,29 +741,19 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         CK(cudaMemcpyAsync(h->l1_start.p, starts.data(), (P1 + 1) * 8, cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemcpyAsync(h->l1_cap.p, caps.data(), P1 * 8, cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemsetAsync(h->l1_fill.p, 0, P1 * 8, h->stream));
-        unsigned long long l2_capacity = 0;
-        if (g.p2) {
-            // sum over buckets of P2 leaves of (mean * slack / 256 + 256) records, mean <= n_b / P2 + 1
-            l2_capacity = exact_leaf.empty()
-                              ? (unsigned long long)(((double)h->l2_slack_num / 256.0) * (double)(l1_total + P)) +
-                                    257ull * P + 1024
-                              : exact_leaf[P];
-            TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
-            TRY(h->l2_base.ensure(P1 * 8));
-            TRY(h->l2_leafcap.ensure(P1 * 4));
-            TRY(h->l2_fill.ensure(P * 8ull));
-            TRY(h->tile_prefix.ensure((P1 + 1) * 8));
-            if (!exact_leaf.empty()) {
-                TRY(h->l2_leaf_start.ensure((P + 1) * 8ull));
-                CK(cudaMemcpyAsync(h->l2_leaf_start.p, exact_leaf.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice,
-                                   h->stream));
-            }
-        }
+        // level-2 records of all buckets: sum over buckets of P2 leaves of
+        // (mean * slack + 256) records, mean <= n_b / P2 + 1
+        const unsigned long long l2_full =
+            g.p2 ? (unsigned long long)(slack * (double)(l1_total + (unsigned long long)P1 * P2)) +
+                       257ull * P1 * P2 + 1024
+                 : 0;
+        const size_t l1_bytes = (size_t)l1_total * 8 * W;
+        const size_t avail = pl.budget > l1_bytes ? pl.budget - l1_bytes : 0;
+        const bool waves = g.p2 && P1 > 1 && (size_t)l2_full * 8 * W > avail;
         if (h->fb_cap < 64) {
             TRY(h->fb_list.ensure(64 * 4));
             h->fb_cap = 64;
         }
-        TRY(h->split_list.ensure((size_t)P * 4));  // every leaf could need key ranges
         TRY(reset_misc(h, out_start));
         Job j{};
         j.g = g;
@@ -642,16 +762,12 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         j.l1_start = h->l1_start.as<unsigned long long>();
         j.l1_cap = h->l1_cap.as<unsigned long long>();
         j.l1_fill = h->l1_fill.as<unsigned long long>();
-        if (g.p2) {
-            j.l2_rec = h->l2_rec.as<unsigned long long>();
-            j.l2_base = h->l2_base.as<unsigned long long>();
-            j.l2_leafcap = h->l2_leafcap.as<unsigned int>();
-            j.l2_fill = h->l2_fill.as<unsigned long long>();
-            j.tile_prefix = h->tile_prefix.as<unsigned long long>();
-            j.l2_leaf_start = exact_leaf.empty() ? nullptr : h->l2_leaf_start.as<unsigned long long>();
-        }
         fill_job_outputs(h, j);
-        j.l2_capacity = exact_leaf.empty() ? l2_capacity : ~0ull;
+        j.l2_slack_num = h->l2_slack_num;
+        if (h->p.flags & KMER_FLAG_BLOOM_GATE) {
+            j.gate = h->gate2.as<unsigned long long>();
+            j.gate_bits = h->gate_bits;
+        }
         // one scatter job per submitted readset, one CTA per 256 reads
         std::vector<Job> sjobs;
         std::vector<unsigned long long> tile_off(1, 0);
@@ -667,90 +783,105 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         TRY(prof_begin(h, kmer_analysis::STG_SCATTER));
         if (!sjobs.empty()) {
             CK(launch_scatter(W, h->d_sjobs.as<Job>(), h->d_tile_off.as<unsigned long long>(), (unsigned)sjobs.size(),
-                              tile_off.back(), g.p1, g.k, h->stream));
+                              tile_off.back(), g.p1, g.k, j.gate != nullptr, h->stream));
             h->st.launches++;
         }
         TRY(prof_end(h, kmer_analysis::STG_SCATTER));
-        const std::vector<unsigned long long> leaf_off = {0ull, (unsigned long long)P};
-        TRY(upload(h, h->d_leaf_off, leaf_off));
-        TRY(h->d_job_tile_off.ensure(2 * 8));
-        // level 2 and leaves may be re-run without re-scattering
-        for (unsigned sub_attempt = 0;; ++sub_attempt) {
-            if (sub_attempt > 8) return fail(KMER_ERR_TABLE_FULL, "leaf buffers still too small after retries");
-            j.l2_capacity = exact_leaf.empty() ? l2_capacity : ~0ull;
-            TRY(upload(h, h->d_ajob, std::vector<Job>{j}));
-            if (g.p2) {
-                CK(cudaMemsetAsync(h->l2_fill.p, 0, P * 8ull, h->stream));
-                TRY(prof_begin(h, kmer_analysis::STG_REPART));
-                CK(launch_l2_plan(h->d_ajob.as<Job>(), 1, h->d_job_tile_off.as<unsigned long long>(), h->stream));
-                CK(launch_repart(W, h->d_ajob.as<Job>(), h->d_job_tile_off.as<unsigned long long>(), 1, g.p2,
-                                 h->num_sms, h->stream));
-                TRY(prof_end(h, kmer_analysis::STG_REPART));
-                h->st.launches += 3;
-            }
-            TRY(prof_begin(h, kmer_analysis::STG_LEAF));
-            CK(launch_leaf(W, h->d_ajob.as<Job>(), h->d_leaf_off.as<unsigned long long>(), 1, P, cap_max, h->num_sms,
-                           h->stream));
-            CK(launch_leaf_split(W, h->d_ajob.as<Job>(), 1, cap_max, h->num_sms, h->stream));
-            TRY(prof_end(h, kmer_analysis::STG_LEAF));
-            h->st.launches += 2;
+        // waves of buckets whose level-2 records fit the budget, from the buckets' fills
+        std::vector<unsigned> wave_start = {0, P1};
+        unsigned long long l2_cap = l2_full;
+        WaveTotals tot;
+        tot.out_n = out_start;
+        if (waves) {
             TRY(read_misc(h));
-            TRY(prof_collect(h));
-            const Misc m = *h->host_misc;
-            if (m.status & ST_L1_OVERFLOW) break;  // re-scatter with exact bucket sizes
-            if (m.status & ST_L2_OVERFLOW) {
-                std::vector<unsigned long long> fill(P);
-                CK(cudaMemcpyAsync(fill.data(), h->l2_fill.p, P * 8ull, cudaMemcpyDeviceToHost, h->stream));
+            if (h->host_misc->status & ST_L1_OVERFLOW) {
+                std::vector<unsigned long long> fill(P1);
+                CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
                 CK(cudaStreamSynchronize(h->stream));
-                h->l2_slack_num = std::min(4096u, h->l2_slack_num * 3 / 2);  // future queries: more slack
-                exact_leaf.assign(P + 1, 0);
-                for (unsigned i = 0; i < P; ++i) exact_leaf[i + 1] = exact_leaf[i] + fill[i];
-                l2_capacity = exact_leaf[P];
-                TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
-                TRY(h->l2_leaf_start.ensure((P + 1) * 8ull));
-                CK(cudaMemcpyAsync(h->l2_leaf_start.p, exact_leaf.data(), (P + 1) * 8ull, cudaMemcpyHostToDevice,
-                                   h->stream));
-                j.l2_rec = h->l2_rec.as<unsigned long long>();
-                j.l2_leaf_start = h->l2_leaf_start.as<unsigned long long>();
+                for (unsigned b = 0; b < P1; ++b) caps[b] = std::max(caps[b], fill[b]);
                 h->st.retries++;
-                TRY(reset_misc(h, out_start, m.stats[2]));
                 continue;
             }
-            if (m.status & (ST_OUT_OVERFLOW | ST_FALLBACK_FULL)) {
-                if (m.status & ST_OUT_OVERFLOW) TRY(ensure_output(h, m.out_n + m.out_n / 16 + 1024, out_start));
-                if (m.status & ST_FALLBACK_FULL) {
-                    TRY(h->fb_list.ensure((m.fb_n + 64) * 4ull));
-                    h->fb_cap = m.fb_n + 64;
+            tot.emitted = h->host_misc->stats[2];
+            std::vector<unsigned long long> fill(P1);
+            CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            const unsigned long long room = std::max<unsigned long long>(avail / (8ull * W), 1);
+            wave_start.assign(1, 0);
+            l2_cap = 0;
+            unsigned long long cur = 0;
+            for (unsigned b = 0; b < P1; ++b) {
+                const unsigned long long need =
+                    (unsigned long long)(slack * (double)(fill[b] + P2)) + 257ull * P2 + 1024;
+                if (b > wave_start.back() && cur + need > room) {
+                    wave_start.push_back(b);
+                    l2_cap = std::max(l2_cap, cur);
+                    cur = 0;
                 }
-                fill_job_outputs(h, j);
-                h->st.retries++;
-                TRY(reset_misc(h, out_start, m.stats[2]));
-                continue;
+                cur += need;
             }
-            TRY(status_error(m.status));
-            h->st.fallback_leaves += m.fb_n;
-            TRY(run_fallbacks(h, j, m.fb_n));
-            const Misc fin = *h->host_misc;
-            if (fin.status & ST_OUT_OVERFLOW) return fail(KMER_ERR_CUDA, "fallback output overflow");
-            if (fin.stats[0] != fin.stats[2])  // every emitted window must be counted by exactly one leaf
-                return fail(KMER_ERR_CUDA, "internal: %llu windows emitted but %llu counted", fin.stats[2],
-                            fin.stats[0]);
-            h->n_out = fin.out_n;
-            h->res_windows += fin.stats[0];
-            h->res_distinct += fin.stats[1];
-            h->st.records_emitted += fin.stats[2];
-            h->st.leaf_splits += fin.stats[3];
-            if (g.p2) h->st.records_l2 += fin.stats[2];
-            return KMER_OK;
+            l2_cap = std::max(l2_cap, cur);
+            wave_start.push_back(P1);
+            h->st.l2_waves += (unsigned)wave_start.size() - 1;
         }
-        // level-1 overflow: take the exact bucket demand and re-scatter
-        std::vector<unsigned long long> fill(P1);
-        CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        for (unsigned b = 0; b < P1; ++b) caps[b] = std::max(caps[b], fill[b]);
-        exact_leaf.clear();
-        h->st.retries++;
+        bool rescatter = false;
+        for (size_t w = 0; w + 1 < wave_start.size() && !rescatter; ++w)
+            TRY(run_level2(h, j, wave_start[w], wave_start[w + 1] - wave_start[w], l2_cap, cap_max, waves, tot,
+                           &rescatter));
+        if (rescatter) {  // level-1 overflow: take the exact bucket demand and re-scatter
+            std::vector<unsigned long long> fill(P1);
+            CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (unsigned b = 0; b < P1; ++b) caps[b] = std::max(caps[b], fill[b]);
+            h->st.retries++;
+            continue;
+        }
+        if (tot.windows != tot.emitted)  // every emitted window must be counted by exactly one leaf
+            return fail(KMER_ERR_CUDA, "internal: %llu windows emitted but %llu counted", tot.emitted, tot.windows);
+        h->n_out = tot.out_n;
+        h->res_windows += tot.windows;
+        h->res_distinct += tot.distinct;
+        h->st.records_emitted += tot.emitted;
+        h->st.leaf_splits += tot.splits;
+        if (g.p2) h->st.records_l2 += tot.emitted;
+        return KMER_OK;
     }
+}
+
+// The Bloom gate's pass over every submitted readset (gate.cu): fills F1 and
+// F2 and returns the valid windows, first sightings and keys seen at least
+// twice.  Filters get 8 bits per expected distinct key (the first sightings
+// per window learned at this k, else one per window).
+int run_gate(kmer_analysis* h, unsigned long long windows, unsigned long long (&c)[3]) {
+    const double ratio = (h->hist_k == h->p.k && h->gate_ratio > 0.0) ? std::min(1.0, 1.15 * h->gate_ratio) : 1.0;
+    const unsigned long long keys = std::max<unsigned long long>(1024, (unsigned long long)(ratio * (double)windows));
+    unsigned bits = 1;
+    while ((1ull << bits) * 64 < keys * 8 && bits < 40) ++bits;
+    h->gate_bits = bits;
+    const size_t bytes = (size_t)8 << bits;
+    TRY(h->gate1.ensure(bytes));
+    TRY(h->gate2.ensure(bytes));
+    TRY(h->gate_cnt.ensure(3 * 8));
+    CK(cudaMemsetAsync(h->gate1.p, 0, bytes, h->stream));
+    CK(cudaMemsetAsync(h->gate2.p, 0, bytes, h->stream));
+    CK(cudaMemsetAsync(h->gate_cnt.p, 0, 3 * 8, h->stream));
+    Job j{};
+    j.g.k = h->p.k;
+    j.g.W = h->W();
+    j.g.hb = 2 * j.g.k - 64 * (j.g.W - 1);
+    TRY(prof_begin(h, kmer_analysis::STG_GATE));
+    for (const kmer_readset* rs : h->submitted) {
+        if (rs->n_reads == 0) continue;
+        set_readset(j, rs);
+        CK(launch_gate(j, h->gate1.as<unsigned long long>(), h->gate2.as<unsigned long long>(), bits,
+                       h->gate_cnt.as<unsigned long long>(), h->stream));
+        h->st.launches++;
+    }
+    TRY(prof_end(h, kmer_analysis::STG_GATE));
+    CK(cudaMemcpyAsync(c, h->gate_cnt.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    TRY(prof_collect(h));
+    return KMER_OK;
 }
 
 int run_direct(kmer_analysis* h, unsigned long long windows) {
@@ -833,13 +964,32 @@ int do_query(kmer_analysis* h) {
             // the records of a pass get what the output leaves of the budget
             const size_t out_bytes = h->ext_out ? 0 : (size_t)(h->out_cap * out_bytes_per);
             h->hint_ratio = h->p.distinct_hint ? std::min(1.0, (double)h->p.distinct_hint / (double)windows) : 0.0;
-            const Plan pl = make_plan(h, windows, budget > 2 * out_bytes ? budget - out_bytes : budget / 2, cap_max);
+            // Bloom gate: the scatter emits only the windows of keys seen twice
+            // (windows - first sightings + keys seen twice, up to false positives)
+            unsigned long long gate_counts[3] = {0, 0, 0}, rec_windows = windows, gated_distinct = 0;
+            size_t rec_budget = budget > 2 * out_bytes ? budget - out_bytes : budget / 2;
+            const bool gated = (h->p.flags & KMER_FLAG_BLOOM_GATE) != 0;
+            if (gated) {
+                TRY(run_gate(h, windows, gate_counts));
+                h->st.gate_first = gate_counts[1];
+                h->st.gate_twice = gate_counts[2];
+                const unsigned long long est = gate_counts[0] - gate_counts[1] + gate_counts[2];
+                rec_windows = std::min(windows, est + est / 32 + 4096);
+                gated_distinct = gate_counts[2];
+                const size_t fb = h->gate1.bytes + h->gate2.bytes;
+                rec_budget = rec_budget > 2 * fb ? rec_budget - fb : rec_budget / 2;
+            }
+            const Plan pl = make_plan(h, rec_windows, rec_budget, cap_max, gated_distinct);
             h->st.pass_bits = pl.g.ps;
             h->st.l1_bits = pl.g.p1;
             h->st.l2_bits = pl.g.p2;
             h->st.leaf_table_slots = cap_max;
             h->st.passes = pl.passes;
             for (unsigned pass = 0; pass < pl.passes; ++pass) TRY(run_pass(h, pl, pass, cap_max));
+            if (gated) {  // every valid window was seen by the gate; the leaves saw the gated ones
+                h->res_windows = gate_counts[0];
+                h->gate_ratio = (double)gate_counts[1] / (double)std::max(1ull, gate_counts[0]);
+            }
         }
     }
     h->out_hint = h->n_out;

@@ -104,7 +104,7 @@ int plan_job(kmer_batch* b, BJob& j) {
     j.basis = std::max<unsigned long long>(basis, 1);
     // one pass (a batch never splits a job into passes: such jobs run alone)
     j.g = plan_geometry(p.k, std::max<unsigned long long>(j.windows, 1), std::max<unsigned long long>(basis, 1),
-                        ~size_t(0) / 4, j.cap_max, p.leaf_bits, p.l1_bits);
+                        ~size_t(0) / 4, j.cap_max, p.leaf_bits, p.l1_bits, false);
     const unsigned P1 = 1u << j.g.p1, P = 1u << (j.g.p1 + j.g.p2);
     const unsigned long long mean = (j.windows + P1 - 1) / P1;
     j.caps.assign(P1, mean + mean / 8 + 1024);
@@ -242,7 +242,7 @@ int capture_wave(kmer_batch* b, Wave& w) {
         if (e == cudaSuccess) e = cudaMemsetAsync(b->misc.as<Misc>() + id, 0, sizeof(Misc), b->stream);
     for (size_t ci = 0; ci < w.classes.size() && e == cudaSuccess; ++ci) {
         const auto& c = w.classes[ci];
-        e = launch_scatter(c.W, dj + c.first, maps + w.tile_off_at[ci], c.count, c.tiles, c.max_p1, c.min_k,
+        e = launch_scatter(c.W, dj + c.first, maps + w.tile_off_at[ci], c.count, c.tiles, c.max_p1, c.min_k, false,
                            b->stream);
     }
     for (size_t ci = 0; ci < w.classes.size() && e == cudaSuccess; ++ci) {

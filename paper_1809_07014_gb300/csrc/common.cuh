@@ -118,7 +118,11 @@ struct Job {
     unsigned long long n_reads;
     Geometry g;
     unsigned pass;
-    // level-1 buckets (P1 = 1 << g.p1)
+    // level-1 buckets (P1 = 1 << g.p1).  The level-2 stages may take a window
+    // of them (a wave): buckets bucket0 .. bucket0 + n_buckets - 1, with the
+    // per-bucket arrays below starting at bucket0 and the level-2 arrays
+    // holding that window only; n_buckets = 0 means all P1 buckets.
+    unsigned bucket0, n_buckets;
     unsigned long long* l1_rec;            // records, W words each
     const unsigned long long* l1_start;    // record index of each bucket
     const unsigned long long* l1_cap;      // capacity (records) of each bucket
@@ -146,6 +150,9 @@ struct Job {
     unsigned int* fb_list;
     unsigned int* fb_n;
     unsigned int fb_cap;
+    // Bloom gate (gate.cu): F2, 2^gate_bits words; null = every window is emitted
+    const unsigned long long* gate;
+    unsigned gate_bits;
     // classification
     unsigned min_count, ext_mode, t_base, err_num, err_den, t_ext;
     // sizing: level-2 leaf capacity = mean * l2_slack_num / 256 + 256 records;
@@ -189,6 +196,9 @@ __device__ inline unsigned char classify_side(const unsigned (&n)[4], unsigned d
 }
 
 __device__ inline void set_status(const Job& j, unsigned bits) { atomicOr(j.status, bits); }
+
+// Level-1 buckets the level-2 stages of a job take (a wave, or all of them).
+__host__ __device__ inline unsigned job_buckets(const Job& j) { return j.n_buckets ? j.n_buckets : 1u << j.g.p1; }
 
 // Index of the job that owns work unit `u`, given the exclusive prefix `off`
 // (n + 1 entries) of the jobs' unit counts (jobs with no units are skipped).

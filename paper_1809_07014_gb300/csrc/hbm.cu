@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const 
         if (rb && ((unsigned)((tail >> 6) >> shift) & rmask) != rs) continue;  // another range
 #pragma unroll
         for (int w = 0; w < W - 1; ++w) key[w] = recs[(start + i) * W + w];
-        const unsigned long long z = record_z(g, j.pass, bucket, tail);
+        const unsigned long long z = record_z(g, j.pass, j.bucket0 + bucket, tail);
         key[W - 1] = z_to_tail<W>(z, key, g.bt);
         if (!hbm_insert<W>(t, cap, key, z, ext_left(tail), ext_right(tail), j.status)) break;
         ++windows;

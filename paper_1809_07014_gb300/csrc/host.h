@@ -135,8 +135,12 @@ void analysis_set_sizing(kmer_analysis_t* h, uint64_t memory_budget, uint64_t di
 // Partition geometry for one analysis: k-mer words, pass bits and level bits.
 // basis = expected distinct keys (or windows), cap_max = leaf table slots,
 // leaf_bits / l1_bits = overrides (0 = automatic).
+// Level-2 waves: the repartition and leaf stages may take the level-1 buckets
+// in up to this many windows, so that only one window's level-2 records are
+// held at a time.
+constexpr unsigned kMaxWaves = 8;
 Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
-                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits);
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves);
 
 }  // namespace kmer
 

@@ -37,13 +37,20 @@ __host__ __device__ inline unsigned fallback_rs(unsigned e) { return e >> (kFbLe
 cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsigned long long n, unsigned* idx,
                                unsigned long long cap, int num_sms, cudaStream_t s);
 
+// Bloom gate (gate.cu): adds every window's key of the job's reads to filter
+// f1, and keys already in f1 to f2 (both 2^log2_words words, zeroed by the
+// caller); counts[0..2] += windows, first sightings, keys entering f2.
+cudaError_t launch_gate(const Job& j, unsigned long long* f1, unsigned long long* f2, unsigned log2_words,
+                        unsigned long long* counts, cudaStream_t s);
+
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
 // tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles; min_k =
 // the smallest k of the jobs (one-word keys with k >= 17 roll on their high
 // half).
 size_t scatter_smem_bytes(unsigned W, unsigned p1);
+// gated: every job carries a Bloom gate (Job::gate) and emits only its keys.
 cudaError_t launch_scatter(unsigned W, const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
-                           unsigned long long tiles, unsigned max_p1, unsigned min_k, cudaStream_t s);
+                           unsigned long long tiles, unsigned max_p1, unsigned min_k, bool gated, cudaStream_t s);
 
 // Per analysis: level-2 tile counts, leaf capacities and leaf region bases;
 // then job_tile_off = prefix of the analyses' level-2 tiles (device array).

@@ -324,7 +324,7 @@ __device__ __forceinline__ void sweep_table(const Job& j, const Table& t, const 
         const unsigned nl[4] = {pl[0] & 0xFFFFu, pl[0] >> 16, pl[1] & 0xFFFFu, pl[1] >> 16};
         const unsigned nr[4] = {pl[2] >> 16, pl[3] & 0xFFFFu, pl[3] >> 16, pl[4] & 0xFFFFu};
         const unsigned c = nl[0] + nl[1] + nl[2] + nl[3] + (pl[2] & 0xFFFFu);
-        const unsigned long long z = record_z(j.g, j.pass, li.bucket, tl);
+        const unsigned long long z = record_z(j.g, j.pass, j.bucket0 + li.bucket, tl);
         key[W - 1] = z_to_tail<W>(z, key, j.g.bt);
 #pragma unroll
         for (int w = 0; w < W; ++w) j.out_keys[pos * W + w] = key[w];

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kStageThreads) l2_plan_kernel(const Job* __res
     const unsigned long long l2_capacity = j.l2_capacity;
     __shared__ unsigned long long warp_tmp[8];
     __shared__ unsigned long long s_tiles, s_slots;
-    const unsigned P1 = 1u << j.g.p1, P2 = 1u << j.g.p2;
+    const unsigned P1 = job_buckets(j), P2 = 1u << j.g.p2;
     const unsigned tile = repart_tile(j.g.W);
     if (threadIdx.x == 0) { s_tiles = 0; s_slots = 0; }
     __syncthreads();
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kStageThreads) job_tiles_kernel(const Job* __r
         if (i < n_jobs) {
             const Job& jb = jobs[i];
             // an analysis whose planner overflowed contributes no tiles (the host retries it)
-            if (jb.g.p2 && !(*(volatile unsigned*)jb.status & ST_L2_PLAN)) t = jb.tile_prefix[1u << jb.g.p1];
+            if (jb.g.p2 && !(*(volatile unsigned*)jb.status & ST_L2_PLAN)) t = jb.tile_prefix[job_buckets(jb)];
         }
         unsigned long long tot;
         const unsigned long long ex = block_scan_u64(t, warp_tmp, &tot);
@@ -134,7 +134,7 @@ __device__ __forceinline__ RepartTile repart_tile_at(const Job* __restrict__ job
     rt.ji = cur.ji;
     const Job& j = jobs[rt.ji];
     const unsigned long long tile = gt - job_tile_off[rt.ji];
-    const unsigned last = (1u << j.g.p1) - 1;
+    const unsigned last = job_buckets(j) - 1;
     // bucket of this tile: last b with tile_prefix[b] <= tile
     unsigned b = cur.bucket;
     if (b != 0xFFFFFFFFu && b < last && j.tile_prefix[b + 1] <= tile) {

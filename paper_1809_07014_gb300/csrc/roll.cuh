@@ -195,6 +195,39 @@ __device__ __forceinline__ bool make_record(const Geometry& g, unsigned pass, co
     return true;
 }
 
+// Bloom-gate hash of a canonical key (gate.cu): the 64-bit finaliser of
+// MurmurHash3 applied to the last word xored with a hash of the head words.
+template <int W>
+__device__ __forceinline__ unsigned long long gate_hash(const unsigned long long (&key)[W]) {
+    unsigned long long h = key[W - 1] ^ head_hash<W>(key) ^ 0x2545F4914F6CDD1Dull;
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    h *= 0xC4CEB9FE1A85EC53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+// The filter word (top log2_words bits of the hash) and four bits within it
+// (four 6-bit fields of the low bits).
+struct GateProbe {
+    unsigned long long word, mask;
+};
+__device__ __forceinline__ GateProbe gate_probe(unsigned long long h, unsigned log2_words) {
+    GateProbe p;
+    p.word = log2_words ? h >> (64 - log2_words) : 0ull;
+    p.mask = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63)) | (1ull << ((h >> 18) & 63));
+    return p;
+}
+
+// The key is in the gate's filter (every bit of its probe set).
+template <int W>
+__device__ __forceinline__ bool gate_has(const unsigned long long* f, unsigned log2_words,
+                                         const unsigned long long (&key)[W]) {
+    const GateProbe p = gate_probe(gate_hash<W>(key), log2_words);
+    return (__ldg(f + p.word) & p.mask) == p.mask;
+}
+
 // z of a record held in a known pass and level-1 bucket.
 __device__ __forceinline__ unsigned long long record_z(const Geometry& g, unsigned pass, unsigned bucket,
                                                        unsigned long long tail) {

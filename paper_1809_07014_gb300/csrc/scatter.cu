@@ -27,7 +27,7 @@ struct L1Dest {
 
 // One CTA: 256 consecutive reads of job j (a read tile).
 // MAXPER: destinations handled by one thread in a flush (fan-out / 256).
-template <int W, unsigned MAXPER, bool HI>
+template <int W, unsigned MAXPER, bool HI, bool GATE>
 __device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long long r0, const unsigned long long r1,
                                              unsigned char* smem) {
     constexpr unsigned R = ScatterShape<W>::R, S = ScatterShape<W>::S;
@@ -52,6 +52,8 @@ __device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long l
     L1Dest dest{j.l1_fill, j.l1_start, j.l1_cap};
     const Geometry g = j.g;
     const unsigned pass = j.pass;
+    const unsigned long long* gate = j.gate;  // Bloom gate (GATE): emit only keys in F2
+    const unsigned gate_bits = j.gate_bits;
     unsigned emitted = 0;
     for (unsigned round = 0; round < rounds; ++round) {
 #pragma unroll 2
@@ -62,7 +64,8 @@ __device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long l
             if (have && t <= L) {
                 unsigned long long key[W], rec[W];
                 unsigned lc = 0, rc = 0, bucket = 0;
-                if (roll.step(t, key, lc, rc) && make_record<W>(g, pass, key, lc, rc, rec, bucket)) {
+                if (roll.step(t, key, lc, rc) && (!GATE || gate_has<W>(gate, gate_bits, key)) &&
+                    make_record<W>(g, pass, key, lc, rc, rec, bucket)) {
                     const unsigned rank = atomicAdd(&b.hist[bucket], 1u);
 #pragma unroll
                     for (int w = 0; w < W; ++w) b.stage[(size_t)e * W + w] = rec[w];
@@ -81,7 +84,7 @@ __device__ __forceinline__ void scatter_tile(const Job& j, const unsigned long l
 }
 
 // One CTA per read tile over all jobs (all of key width W).
-template <int W, unsigned MAXPER, bool HI>
+template <int W, unsigned MAXPER, bool HI, bool GATE>
 __global__ void __launch_bounds__(kStageThreads, W == 1 ? 3 : 2)
 scatter_kernel(const Job* __restrict__ jobs, const unsigned long long* __restrict__ tile_off, const unsigned n_jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -90,7 +93,7 @@ scatter_kernel(const Job* __restrict__ jobs, const unsigned long long* __restric
     const Job& j = jobs[ji];
     const unsigned long long r0 = (t - tile_off[ji]) * kStageThreads;
     const unsigned long long r1 = r0 + kStageThreads < j.n_reads ? r0 + kStageThreads : j.n_reads;
-    scatter_tile<W, MAXPER, HI>(j, r0, r1, smem);
+    scatter_tile<W, MAXPER, HI, GATE>(j, r0, r1, smem);
 }
 
 size_t scatter_smem_bytes(unsigned W, unsigned p1) {
@@ -103,39 +106,46 @@ size_t scatter_smem_bytes(unsigned W, unsigned p1) {
     }
 }
 
-template <int W, unsigned MAXPER, bool HI>
-static cudaError_t launch_scatter_wp(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
-                                     unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+template <int W, unsigned MAXPER, bool HI, bool GATE>
+static cudaError_t launch_scatter_wpg(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                                      unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
     const size_t smem = scatter_smem_bytes(W, max_p1);
-    cudaError_t e =
-        cudaFuncSetAttribute(scatter_kernel<W, MAXPER, HI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<W, MAXPER, HI, GATE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (tiles == 0) return cudaSuccess;
     if (tiles > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    scatter_kernel<W, MAXPER, HI><<<(unsigned)tiles, kStageThreads, smem, s>>>(jobs, tile_off, n_jobs);
+    scatter_kernel<W, MAXPER, HI, GATE><<<(unsigned)tiles, kStageThreads, smem, s>>>(jobs, tile_off, n_jobs);
     return cudaGetLastError();
+}
+
+template <int W, unsigned MAXPER, bool HI>
+static cudaError_t launch_scatter_wp(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
+                                     unsigned long long tiles, unsigned max_p1, bool gated, cudaStream_t s) {
+    return gated ? launch_scatter_wpg<W, MAXPER, HI, true>(jobs, tile_off, n_jobs, tiles, max_p1, s)
+                 : launch_scatter_wpg<W, MAXPER, HI, false>(jobs, tile_off, n_jobs, tiles, max_p1, s);
 }
 
 template <int W, bool HI>
 static cudaError_t launch_scatter_w(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
-                                    unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
+                                    unsigned long long tiles, unsigned max_p1, bool gated, cudaStream_t s) {
     // MAXPER: destinations of one thread in a flush (fan-out / 256, rounded up to 2, 4 or 8)
     if ((1u << max_p1) <= 2 * kStageThreads)
-        return launch_scatter_wp<W, 2, HI>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+        return launch_scatter_wp<W, 2, HI>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
     if ((1u << max_p1) <= 4 * kStageThreads)
-        return launch_scatter_wp<W, 4, HI>(jobs, tile_off, n_jobs, tiles, max_p1, s);
-    return launch_scatter_wp<W, kMaxStageDest / kStageThreads, HI>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+        return launch_scatter_wp<W, 4, HI>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
+    return launch_scatter_wp<W, kMaxStageDest / kStageThreads, HI>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
 }
 
 cudaError_t launch_scatter(unsigned W, const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
-                           unsigned long long tiles, unsigned max_p1, unsigned min_k, cudaStream_t s) {
+                           unsigned long long tiles, unsigned max_p1, unsigned min_k, bool gated, cudaStream_t s) {
     switch (W) {
         case 1:
-            return min_k >= 17 ? launch_scatter_w<1, true>(jobs, tile_off, n_jobs, tiles, max_p1, s)
-                               : launch_scatter_w<1, false>(jobs, tile_off, n_jobs, tiles, max_p1, s);
-        case 2: return launch_scatter_w<2, false>(jobs, tile_off, n_jobs, tiles, max_p1, s);
-        case 3: return launch_scatter_w<3, false>(jobs, tile_off, n_jobs, tiles, max_p1, s);
-        case 4: return launch_scatter_w<4, false>(jobs, tile_off, n_jobs, tiles, max_p1, s);
+            return min_k >= 17 ? launch_scatter_w<1, true>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s)
+                               : launch_scatter_w<1, false>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
+        case 2: return launch_scatter_w<2, false>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
+        case 3: return launch_scatter_w<3, false>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
+        case 4: return launch_scatter_w<4, false>(jobs, tile_off, n_jobs, tiles, max_p1, gated, s);
     }
     return cudaErrorInvalidValue;
 }

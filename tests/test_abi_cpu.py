@@ -52,10 +52,21 @@ def test_default_params(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("k", 0), ("k", 2), ("k", 128), ("k", 129), ("min_count", 0), ("err_den", 0), ("ext_mode", 2),
-    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 2), ("l1_bits", 12),
+    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 4), ("l1_bits", 12),
 ])
 def test_invalid_params_rejected_before_device(lib, field, value):
     p = pkg.make_params(31)
+    setattr(p, field, value)
+    with pytest.raises(pkg.KmerError) as e:
+        pkg.kmer_analysis_create(p)
+    assert e.value.code == pkg.KMER_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [("min_count", 1), ("variant", 1)])
+def test_bloom_gate_needs_min_count_two_and_partitions(lib, field, value):
+    """The gate drops k-mers seen once, so it is exact only for min_count >= 2,
+    and it feeds the partitioned variant's scatter."""
+    p = pkg.make_params(31, flags=pkg.KMER_FLAG_BLOOM_GATE)
     setattr(p, field, value)
     with pytest.raises(pkg.KmerError) as e:
         pkg.kmer_analysis_create(p)
