@@ -36,6 +36,8 @@ METRIC = "canonical k-mers/sec"
 UNIT = "k-mers/s"
 ORACLE_SAMPLE_READS = 200_000  # cpu_baseline sample: about 10-20 s of oracle work on every host core
 REF_STEP_READS = 60_000        # reference arm: reads per timed step (a few seconds each on every host core)
+EXTRA_SCALE = 0.25             # sub-records of the default line: batched and served workloads at this size
+EXTRA_REQUESTS = 24
 
 
 def parse_args():
@@ -55,18 +57,20 @@ def parse_args():
     ap.add_argument("--tune", choices=["auto", "hints", "none"], default="auto",
                     help="batched: autotuned geometry and hints, sizing hints only, or no hints")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
-    ap.add_argument("--large", action="store_true",
-                    help="serve: also run the 15-Gbase, 500-genome instance at k=55 within a 180 GB budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-threads", type=int, default=3, help="host threads of the end-to-end pipeline")
     ap.add_argument("--e2e-steps", type=int, default=24,
                     help="end-to-end steps of the several-thread run (at least --steps): the pipeline "
                          "fills and drains once per run")
+    ap.add_argument("--e2e-repeats", type=int, default=3, help="end-to-end runs of the several-thread pipeline "
+                                                                "(the median is reported)")
     ap.add_argument("--e2e-io", choices=["staged", "in-place"], default="staged",
                     help="end to end with several threads: host buffers moved by the copy engines "
                          "(KMER_HOST_STAGED, the counting of one step at a time) or read and written in "
                          "place by the kernels (KMER_HOST)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single: leave out the batched, serving and multi-k sub-records of the default line")
     return ap.parse_args()
 
 
@@ -449,24 +453,31 @@ def run_ours(args):
         run_lane(lanes[0], args.steps, False)
         torch.cuda.synchronize()
         dt1, w1 = reduce_over_ranks(time.perf_counter() - t0, lanes[0]["windows"], dev)
-        # several threads taking turns
+        # several threads taking turns; the run is repeated and its median reported
+        # (the host side makes single runs vary)
         e2e_steps = max(args.steps, args.e2e_steps)
-        for ln in lanes:
-            ln["windows"] = ln["d2h"] = 0
-        barrier()
-        t0 = time.perf_counter()
-        ths = [threading.Thread(target=run_lane, args=(lanes[i], (e2e_steps + n_thr - 1 - i) // n_thr, staged, i))
-               for i in range(n_thr)]
-        for th in ths:
-            th.start()
-        for th in ths:
-            th.join()
-        torch.cuda.synchronize()
-        wins = sum(ln["windows"] for ln in lanes)
-        dt2, w2 = reduce_over_ranks(time.perf_counter() - t0, wins, dev)
+        reps = []
+        for _ in range(max(1, args.e2e_repeats)):
+            for ln in lanes:
+                ln["windows"] = ln["d2h"] = 0
+            barrier()
+            t0 = time.perf_counter()
+            ths = [threading.Thread(target=run_lane,
+                                    args=(lanes[i], (e2e_steps + n_thr - 1 - i) // n_thr, staged, i))
+                   for i in range(n_thr)]
+            for th in ths:
+                th.start()
+            for th in ths:
+                th.join()
+            torch.cuda.synchronize()
+            wins = sum(ln["windows"] for ln in lanes)
+            dt_r, w_r = reduce_over_ranks(time.perf_counter() - t0, wins, dev)
+            reps.append((w_r / dt_r, dt_r, w_r, sum(ln["d2h"] for ln in lanes)))
+        rate2, dt2, w2, d2h = sorted(reps)[len(reps) // 2]
         h2d = 2 * n_bases + 8 * (n_reads + 1)
-        line["e2e"] = {"value": w2 / dt2, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": sum(ln["d2h"] for ln in lanes) // e2e_steps,
+        line["e2e"] = {"value": rate2, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h // e2e_steps, "repeats": [round(r[0] / 1e9, 2) for r in reps],
+                       "repeat_unit": "G k-mers/s", "median_of": len(reps),
                        "ms_per_step": 1e3 * dt2 / e2e_steps, "steps": e2e_steps, "host_threads": n_thr,
                        "host_io": ("KMER_HOST_STAGED (copy engines), one step counting at a time" if staged
                                    else "KMER_HOST (in place)"),
@@ -487,10 +498,30 @@ def run_ours(args):
                                 "sample": f"first {n} reads ({w} windows) of the same workload, sharded oracle "
                                           f"(one FNV-1a shard per core, each walking every read), {dt:.1f} s on "
                                           f"{cores} host cores"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     ka.close()
     rset.close()
+    del bases_d, quals_d, offs_d
+    # ---- the batched, served and multi-k forms on the same GPU (rank 0 at N = 1),
+    # at reduced sizes so that the default run stays within minutes
+    if rank == 0 and world == 1 and not args.no_extras:
+        torch.cuda.synchronize()
+        b = batched_record(EXTRA_SCALE, 3, 2, "hints")
+        line["batched"] = {"value": b["value"], "unit": UNIT, "ms_per_run": round(b["ms_per_step"], 2),
+                           "workload": b["config"]["workload"], "bases": b["config"]["bases"],
+                           "single_instance": {"value": b["single_instance"]["value"],
+                                               "ms_total": round(b["single_instance"]["ms_total"], 2)},
+                           "speedup_vs_single_instance": round(b["speedup_vs_single_instance"], 4),
+                           "waves": b["batch_stats"]["waves"], "graph_launches": b["batch_stats"]["graph_launches"]}
+        sv = serve_record(EXTRA_SCALE, EXTRA_REQUESTS)
+        line["serve"] = {"value": sv["value"], "unit": UNIT, "latency_ms": sv["latency_ms"],
+                         "workload": sv["config"]["workload"], "one_at_a_time": sv["one_at_a_time"]["value"],
+                         "saturated": sv["saturated"]["value"], "peak_running": sv["peak_running"]}
+        mk = multik_record(5, 3)
+        line["multik"] = {"value": mk["value"], "unit": UNIT, "ms_per_round_batch": mk["batch"]["ms_per_round"],
+                          "ms_per_round_sequential": mk["sequential"]["ms_per_round"],
+                          "per_k_ms_sequential": mk["sequential"]["per_k_ms"], "workload": mk["config"]["workload"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
@@ -513,7 +544,9 @@ def batch_workload(scale: float):
     return recipes
 
 
-def run_batched(args):
+def batched_record(scale: float, steps: int, warmup: int, tune: str) -> dict:
+    """The 64-sample batch (one graph per wave) against the same jobs run as
+    one regular query each, back to back, on the same GPU."""
     import numpy as np
     import torch
 
@@ -523,7 +556,7 @@ def run_batched(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    recipes = batch_workload(args.scale)
+    recipes = batch_workload(scale)
     rsets, ks = [], []
     t0 = time.perf_counter()
     for r, k in recipes:
@@ -546,7 +579,7 @@ def run_batched(args):
         ka.close()
     # autotune per k on the median-size job of that k
     tunings = {}
-    if args.tune != "none":
+    if tune != "none":
         for k in sorted(set(ks)):
             idx = [i for i in range(len(ks)) if ks[i] == k]
             mid = sorted(idx, key=lambda i: rsets[i].n_bases)[len(idx) // 2]
@@ -555,28 +588,28 @@ def run_batched(args):
     for rs, k in zip(rsets, ks):
         w = rs.n_bases  # windows of 150-bp reads are ~ (150-k+1)/150 of the bases
         w = int(w * (150 - k + 1) / 150)
-        if args.tune == "none":
+        if tune == "none":
             jobs.append((rs, {"k": k}))
-        elif args.tune == "hints":
+        elif tune == "hints":
             t = tunings[k].params(w)
             jobs.append((rs, {"k": k, "distinct_hint": t["distinct_hint"], "survivors_hint": t["survivors_hint"]}))
         else:
             jobs.append((rs, tunings[k].params(w)))
     b = pkg.Batch(jobs, stream=stream)
-    for _ in range(max(2, args.warmup)):  # the first run may teach the batch its sizing (a re-plan)
+    for _ in range(max(2, warmup)):  # the first run may teach the batch its sizing (a re-plan)
         b.run()
     t1 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.run()
     torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t1) / args.steps
+    t_batch = (time.perf_counter() - t1) / steps
     st = b.stats()
-    line = {"metric": METRIC, "value": windows_all / t_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": windows_all / t_batch, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"batched: {len(jobs)} synthetic metagenome samples, sizes log-uniform "
-                                   f"{5 * args.scale:g}-{500 * args.scale:g} Mbases, k in {{21,33,55}}",
-                       "bases": int(sum(r.n_bases for r in rsets)), "windows": windows_all, "tune": args.tune},
+                                   f"{5 * scale:g}-{500 * scale:g} Mbases, k in {{21,33,55}}",
+                       "bases": int(sum(r.n_bases for r in rsets)), "windows": windows_all, "tune": tune},
             "batch_stats": st,
             "single_instance": {"value": windows_all / t_single, "ms_total": 1e3 * t_single,
                                 "note": "the same jobs, one regular query each, back to back"},
@@ -584,8 +617,15 @@ def run_batched(args):
             "tuning": {k: {"keys_per_leaf": round(t.keys_per_leaf, 1), "l1_shift": t.l1_shift,
                            "distinct_ratio": round(t.distinct_ratio, 4)} for k, t in tunings.items()},
             "setup_s": round(gen_s, 1)}
-    print(json.dumps(line), flush=True)
     b.close()
+    for rs in rsets:
+        rs.close()
+    return line
+
+
+def run_batched(args):
+    print(json.dumps(batched_record(args.scale, args.steps, args.warmup, args.tune)), flush=True)
+
 
 
 # ----------------------------------------------------------------- serving
@@ -594,7 +634,9 @@ def pctl(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=float), q)) if xs else None
 
 
-def run_serve(args):
+def serve_record(scale: float, n_requests: int) -> dict:
+    """Serving: Poisson arrivals at 75 % of the measured one-at-a-time capacity,
+    admitted by footprint on four workers; p50/p99 latency from submit to results."""
     import threading
 
     import numpy as np
@@ -606,7 +648,7 @@ def run_serve(args):
     torch.cuda.set_device(0)
     rng = np.random.default_rng(5)
     n_pool = 12
-    sizes = np.exp(rng.uniform(np.log(1e6), np.log(2e9), n_pool)) * args.scale
+    sizes = np.exp(rng.uniform(np.log(1e6), np.log(2e9), n_pool)) * scale
     pool = []
     t0 = time.perf_counter()
     for i, sz in enumerate(sizes):
@@ -615,7 +657,7 @@ def run_serve(args):
         pool.append(pkg.ReadSet(s.bases, s.quals, s.offsets))
     gen_s = time.perf_counter() - t0
     kset = [21, 33, 55, 77, 99]
-    reqs = [(int(rng.integers(n_pool)), int(rng.choice(kset))) for _ in range(args.requests)]
+    reqs = [(int(rng.integers(n_pool)), int(rng.choice(kset))) for _ in range(n_requests)]
     windows_of = lambda i, k: int(pool[i].n_bases * (150 - k + 1) / 150)
     # capacity: one request at a time, every request of the plan (warm analyses)
     srv = pkg.Server(workers=1)
@@ -680,33 +722,20 @@ def run_serve(args):
             "ms_per_step": 1e3 * span / len(reqs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"serving: {len(reqs)} Poisson requests at 75% of measured capacity, sizes "
-                                   f"log-uniform {args.scale:g}-{2000 * args.scale:g} Mbases, k in {kset}",
+                                   f"log-uniform {scale:g}-{2000 * scale:g} Mbases, k in {kset}",
                        "pool_bases": int(sum(r.n_bases for r in pool)), "workers": 4},
             "latency_ms": {"p50": pctl(lat, 50), "p99": pctl(lat, 99), "max": max(lat)},
             "one_at_a_time": {"value": capacity, "note": "the same requests, one worker, back to back"},
             "saturated": {"value": sat_w / t_sat, "peak_running": peak_sat,
                           "note": "the same requests all queued at once, 4 workers"},
             "peak_running": st["peak_running"], "setup_s": round(gen_s, 1)}
-    if args.large:
-        r = synth.Recipe("metagenome-500-genomes-15Gbases", seed=55, n_genomes=500, genome_len_min=1_000_000,
-                         genome_len_max=5_000_000, abundance_sigma=1.5, n_reads=100_000_000, subst_rate=0.01,
-                         err_qual_lo=2, err_qual_hi=12, n_rate=1e-4)
-        t2 = time.perf_counter()
-        s = synth.generate(r)
-        big = pkg.ReadSet(s.bases, s.quals, s.offsets)
-        del s
-        gen2 = time.perf_counter() - t2
-        srv = pkg.Server(memory_budget=180 * 10**9, workers=1)
-        rid = srv.submit(big, 55)
-        v, info = srv.wait(rid)
-        line["large_instance"] = {"bases": big.n_bases, "k": 55, "windows": int(v.windows),
-                                  "distinct": int(v.distinct), "survivors": int(v.n),
-                                  "latency_ms": info["t_done_ms"] - info["t_submit_ms"],
-                                  "k-mers/s": int(v.windows) / ((info["t_done_ms"] - info["t_start_ms"]) / 1e3),
-                                  "budget_bytes": 180 * 10**9, "setup_s": round(gen2, 1)}
-        srv.release(rid)
-        srv.close()
-    print(json.dumps(line), flush=True)
+    for rs in pool:
+        rs.close()
+    return line
+
+
+def run_serve(args):
+    print(json.dumps(serve_record(args.scale, args.requests)), flush=True)
 
 
 # ------------------------------------------------------------- large instance
@@ -799,9 +828,11 @@ def run_large(args):
 
 
 # ------------------------------------------------------------- multi-k
-def run_multik(args):
-    """The single-genome reads (20 000 x 150 bp) resident on the device, analysed
-    at k = 21, 33, 55, 77, 99 in sequence (Algorithm 1's k loop)."""
+def multik_record(steps: int, warmup: int) -> dict:
+    """The single-genome reads (20 000 x 150 bp) resident on the device,
+    analysed at k = 21, 33, 55, 77, 99 (Algorithm 1's k loop): as five
+    regular queries in sequence, and as one batch of five jobs (one CUDA graph
+    per wave, one launch per stage and key width)."""
     import torch
 
     import synth
@@ -815,7 +846,7 @@ def run_multik(args):
     handles = {k: pkg.KmerAnalysis(k, stream=stream) for k in ks}
     cold = {}
     for k in ks:  # warm-up: allocations and learned sizing; the first query of a handle is timed
-        for i in range(max(3, args.warmup)):
+        for i in range(max(3, warmup)):
             torch.cuda.synchronize()
             tw = time.perf_counter()
             handles[k].reset(); handles[k].submit(rs); handles[k].query()
@@ -824,7 +855,7 @@ def run_multik(args):
     torch.cuda.synchronize()
     per_k, windows = {}, 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         for k in ks:
             t1 = time.perf_counter()
             ka = handles[k]
@@ -833,18 +864,37 @@ def run_multik(args):
             per_k.setdefault(k, []).append(time.perf_counter() - t1)
             windows += int(v.windows)
     dt = time.perf_counter() - t0
-    line = {"metric": METRIC, "value": windows / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "multi-k on the single-genome reads: 20 000 x 150 bp from a 100 kbp genome, "
-                                   "resident, k = 21, 33, 55, 77, 99 in sequence (a step = the five analyses)",
-                       "bases": int(rs.n_bases), "l2": "inputs fit the 129 MB L2"},
-            "per_k_ms": {k: round(1e3 * statistics.median(v), 3) for k, v in per_k.items()},
-            "cold_per_k_ms": cold}
-    print(json.dumps(line), flush=True)
     for ka in handles.values():
         ka.close()
+    # the same five analyses as one batch
+    b = pkg.Batch([(rs, {"k": k}) for k in ks], stream=stream)
+    for _ in range(max(3, warmup)):
+        b.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.run()
+    torch.cuda.synchronize()
+    dtb = time.perf_counter() - t0
+    bst = b.stats()
+    b.close()
+    line = {"metric": METRIC, "value": windows / dtb, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * dtb / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "multi-k on the single-genome reads: 20 000 x 150 bp from a 100 kbp genome, "
+                                   "resident, k = 21, 33, 55, 77, 99 (a step = the five analyses)",
+                       "bases": int(rs.n_bases), "l2": "inputs fit the 129 MB L2"},
+            "batch": {"ms_per_round": round(1e3 * dtb / steps, 3), "graph_launches": bst["graph_launches"],
+                      "waves": bst["waves"]},
+            "sequential": {"value": windows / dt, "ms_per_round": round(1e3 * dt / steps, 3),
+                           "per_k_ms": {k: round(1e3 * statistics.median(v), 3) for k, v in per_k.items()},
+                           "cold_per_k_ms": cold}}
     rs.close()
+    return line
+
+
+def run_multik(args):
+    print(json.dumps(multik_record(args.steps, args.warmup)), flush=True)
 
 
 def main():
