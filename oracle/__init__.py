@@ -71,6 +71,9 @@ def _load():
                                                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                          ctypes.c_uint32, ctypes.POINTER(_Result)]
             lib.oracle_kmer_analysis_threads.restype = ctypes.c_int
+            lib.oracle_merge_contigs.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(_Params), vp, vp,
+                                                 ctypes.c_uint64, ctypes.POINTER(_Result)]
+            lib.oracle_merge_contigs.restype = ctypes.c_int
             lib.oracle_free.argtypes = [ctypes.POINTER(_Result)]
             lib.oracle_free.restype = None
             lib.oracle_fnv1a.argtypes = [ctypes.c_char_p, ctypes.c_uint64]
@@ -180,6 +183,28 @@ def run_threads(bases, quals, offsets, params: Params, shard_lo: int = 0, shard_
                                           ctypes.c_void_p(q.ctypes.data if len(q) else 0),
                                           ctypes.c_void_p(o.ctypes.data), n_reads, ctypes.byref(cp),
                                           shard_lo, shard_hi, n_shards, max(1, threads), ctypes.byref(res))
+    return _collect(lib, res, rc, params.k)
+
+
+def merge_contigs(bases, quals, offsets, params: Params, contigs, contig_offsets) -> Result:
+    """Merge of Algorithm 1: the reads' k-mer set (`run`) with the k-mers of the
+    contigs (bytes, offsets), k-mers in both kept once with the reads' record,
+    contig-only k-mers added with count 0 and the classes of their contig
+    neighbours (see kmer_oracle.cpp)."""
+    lib = _load()
+    b, q, o, n_reads = _inputs(bases, quals, offsets)
+    c = _as_u8(contigs)
+    co = np.ascontiguousarray(contig_offsets, dtype=np.uint64)
+    n_contigs = len(co) - 1
+    if n_contigs < 0 or (n_contigs and int(co[-1]) > len(c)):
+        raise ValueError("contig offsets do not match the contig buffer")
+    res = _Result()
+    cp = params._c()
+    rc = lib.oracle_merge_contigs(ctypes.c_void_p(b.ctypes.data if len(b) else 0),
+                                  ctypes.c_void_p(q.ctypes.data if len(q) else 0),
+                                  ctypes.c_void_p(o.ctypes.data), n_reads, ctypes.byref(cp),
+                                  ctypes.c_void_p(c.ctypes.data if len(c) else 0), ctypes.c_void_p(co.ctypes.data),
+                                  n_contigs, ctypes.byref(res))
     return _collect(lib, res, rc, params.k)
 
 

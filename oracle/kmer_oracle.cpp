@@ -45,6 +45,7 @@
 #include <cstring>
 #include <map>
 #include <queue>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -72,6 +73,10 @@ typedef struct {
     uint64_t windows;  /* valid windows counted (in this shard) */
     uint64_t distinct; /* distinct canonical k-mers before the count filter */
 } oracle_result;
+
+void oracle_free(oracle_result *r);
+int oracle_kmer_analysis(const char *bases, const uint8_t *quals, const uint64_t *offsets, uint64_t n_reads,
+                         const oracle_params *p, uint32_t shard, uint32_t n_shards, oracle_result *out);
 
 }  // extern "C"
 
@@ -316,6 +321,90 @@ extern "C" int oracle_kmer_analysis_threads(const char *bases, const uint8_t *qu
         if (++h.first != h.second) heads.push(h);
     }
     return write_result(all, windows, *p, out);
+}
+
+/* Merge of Algorithm 1 (Sec. II-G): the k-mer set of the reads (the
+ * definition above, with its count filter) and ExtractKmers(C, k), the
+ * k-mers of the contigs C, which the paper treats as error-free k-mers with
+ * unique high-quality extensions.  Reading taken here:
+ *  - a contig k-mer's extension on a side is the contig's neighbouring base
+ *    there (none at a contig end), in the k-mer's canonical orientation;
+ *    over all its occurrences in C a side has a set of such bases: one base
+ *    makes the side UNIQUE, none DEAD_END, two or more FORK (every contig base
+ *    is high quality, so no count threshold applies);
+ *  - a k-mer in both sets is kept once, with the reads' record;
+ *  - a k-mer only in the contigs is added with count 0, zero tallies and the
+ *    classes above.
+ * The result is ascending by key. */
+extern "C" int oracle_merge_contigs(const char *bases, const uint8_t *quals, const uint64_t *offsets,
+                                    uint64_t n_reads, const oracle_params *p, const char *contigs,
+                                    const uint64_t *coffsets, uint64_t n_contigs, oracle_result *out) {
+    if (!p || !out || (n_contigs && (!contigs || !coffsets))) return -1;
+    oracle_result reads{};
+    int rc = oracle_kmer_analysis(bases, quals, offsets, n_reads, p, 0, 1, &reads);
+    if (rc) {
+        oracle_free(&reads);
+        return rc;
+    }
+    const size_t k = p->k;
+    // k-mers of the contigs and their neighbour sets (every contig base counts as high quality)
+    oracle_params cp = *p;
+    cp.qual_offset = 0;
+    cp.qual_threshold = 0;
+    std::map<std::string, std::set<int>[2]> ck;
+    for (uint64_t c = 0; c < n_contigs; ++c) {
+        const std::string contig(contigs + coffsets[c], contigs + coffsets[c + 1]);
+        const std::vector<uint8_t> q(contig.size(), 0);
+        walk_read(contig, q.data(), k, cp, [&](const std::string &key, int left, int right) {
+            auto &sides = ck[key];
+            if (left >= 0) sides[0].insert(left);
+            if (right >= 0) sides[1].insert(right);
+        });
+    }
+    // union: the reads' records, then the contig-only k-mers
+    std::map<std::string, size_t> from_reads;  // key -> row of `reads`
+    for (uint64_t j = 0; j < reads.n; ++j) from_reads[std::string(reads.keys + j * k, reads.keys + (j + 1) * k)] = j;
+    std::vector<std::string> added;
+    for (const auto &kv : ck)
+        if (!from_reads.count(kv.first)) added.push_back(kv.first);
+    const uint64_t n = reads.n + added.size();
+    out->n = n;
+    out->windows = reads.windows;
+    out->distinct = reads.distinct;
+    out->keys = (char *)std::malloc(n * k + 1);
+    out->count = (uint64_t *)std::malloc(sizeof(uint64_t) * (n + 1));
+    out->ext = (uint64_t *)std::malloc(sizeof(uint64_t) * (8 * n + 1));
+    out->cls = (uint8_t *)std::malloc(2 * n + 1);
+    if (!out->keys || !out->count || !out->ext || !out->cls) {
+        oracle_free(&reads);
+        return -2;
+    }
+    // ascending merge of the two sorted lists
+    uint64_t i = 0, a = 0, o = 0;
+    while (i < reads.n || a < added.size()) {
+        const bool take_read =
+            a == added.size() || (i < reads.n && std::string(reads.keys + i * k, reads.keys + (i + 1) * k) < added[a]);
+        if (take_read) {
+            std::memcpy(out->keys + o * k, reads.keys + i * k, k);
+            out->count[o] = reads.count[i];
+            for (int e = 0; e < 8; ++e) out->ext[8 * o + e] = reads.ext[8 * i + e];
+            out->cls[2 * o] = reads.cls[2 * i];
+            out->cls[2 * o + 1] = reads.cls[2 * i + 1];
+            ++i;
+        } else {
+            const auto &sides = ck[added[a]];
+            std::memcpy(out->keys + o * k, added[a].data(), k);
+            out->count[o] = 0;
+            for (int e = 0; e < 8; ++e) out->ext[8 * o + e] = 0;
+            for (int s2 = 0; s2 < 2; ++s2)
+                out->cls[2 * o + s2] = sides[s2].empty() ? DEAD_END
+                                                         : (sides[s2].size() == 1 ? (uint8_t)*sides[s2].begin() : FORK);
+            ++a;
+        }
+        ++o;
+    }
+    oracle_free(&reads);
+    return 0;
 }
 
 extern "C" void oracle_free(oracle_result *r) {

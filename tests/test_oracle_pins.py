@@ -405,3 +405,90 @@ def test_threaded_mode_equals_single_thread_on_a_metagenome_slice():
     assert sum(x.distinct for x in parts) == one.distinct
     merged = sorted(r for x in parts for r in as_rows(x))
     assert merged == as_rows(one)
+
+
+# ------------------------------------------------------ merge with contig k-mers
+def contig_kmers_brute(contigs, k):
+    """ExtractKmers of Algorithm 1, written out: canonical k-mer -> the sets of
+    its left and right neighbours over all occurrences in the contigs."""
+    table = {}
+    for c in contigs:
+        c = c.decode() if isinstance(c, bytes) else c
+        for i in range(len(c) - k + 1):
+            w = c[i:i + k]
+            if any(ch not in ORDER for ch in w):
+                continue
+            left = c[i - 1] if i > 0 else None
+            right = c[i + k] if i + k < len(c) else None
+            rc = "".join(COMP[ch] for ch in reversed(w))
+            if rc < w:
+                w, left, right = rc, (COMP.get(right) if right else None), (COMP.get(left) if left else None)
+            sides = table.setdefault(w, (set(), set()))
+            if left is not None and left in ORDER:
+                sides[0].add(left)
+            if right is not None and right in ORDER:
+                sides[1].add(right)
+    return table
+
+
+def merge_brute(reads, contigs, p):
+    rows, _, _ = brute_force(reads, p)
+    have = {r[0] for r in rows}
+    out = list(rows)
+    for key, (ls, rs) in contig_kmers_brute(contigs, p.k).items():
+        if key in have:
+            continue
+        cl = tuple(5 if not s else (ORDER.index(next(iter(s))) if len(s) == 1 else 4) for s in (ls, rs))
+        out.append((key, 0, [0] * 8, cl))
+    return sorted(out, key=lambda r: r[0])
+
+
+def flat(seqs):
+    data = b"".join(seqs)
+    offs = np.zeros(len(seqs) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(x) for x in seqs], dtype=np.uint64)
+    return data, offs
+
+
+def test_merge_hand_case():
+    """Reads ACGTACGTTG, contig AAAAC, k = 3, min_count 1: AAA is new (left
+    neighbour A once; right neighbours A and C: a fork), AAC is in both and
+    keeps the reads' count 1."""
+    bases, offs = flat([b"ACGTACGTTG"])
+    c, co = flat([b"AAAAC"])
+    res = oracle.merge_contigs(bases, b"I" * 10, offs, oracle.Params(k=3, min_count=1), c, co)
+    assert [x.decode() for x in res.keys] == ["AAA", "AAC", "ACG", "CAA", "GTA"]
+    assert list(res.count) == [0, 1, 4, 1, 2]
+    assert tuple(res.cls[0]) == (0, oracle.FORK)
+    assert list(res.ext[0]) == [0] * 8
+
+
+def test_merge_with_no_contigs_changes_nothing():
+    rs = synth.generate(synth.SINGLE_GENOME.scaled(300))
+    p = oracle.Params(k=21)
+    want = oracle.run(rs.bases, rs.quals, rs.offsets, p)
+    got = oracle.merge_contigs(rs.bases, rs.quals, rs.offsets, p, b"", np.zeros(1, dtype=np.uint64))
+    assert as_rows(got) == as_rows(want)
+
+
+def test_merge_with_the_reads_as_contigs_adds_nothing_at_min_count_one():
+    rs = synth.generate(synth.SINGLE_GENOME.scaled(200))
+    p = oracle.Params(k=21, min_count=1)
+    want = oracle.run(rs.bases, rs.quals, rs.offsets, p)
+    got = oracle.merge_contigs(rs.bases, rs.quals, rs.offsets, p, rs.bases, rs.offsets)
+    assert as_rows(got) == as_rows(want)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_merge_against_brute_force(seed):
+    rng = random.Random(3000 + seed)
+    reads = random_reads(rng, rng.randint(0, 12), 1, 30, alphabet=rng.choice(["ACGT", "AC"]), n_rate=0.02)
+    contigs = [r[0] for r in random_reads(rng, rng.randint(0, 6), 1, 40, alphabet=rng.choice(["ACGT", "AC"]),
+                                          n_rate=0.02)]
+    k = rng.choice([1, 3, 5, 7])
+    p = oracle.Params(k=k, min_count=rng.choice([1, 2]), ext_mode=rng.choice([0, 1]))
+    bases, offs = flat([r[0] for r in reads])
+    quals = b"".join(r[1] for r in reads)
+    c, co = flat(contigs)
+    got = oracle.merge_contigs(bases, quals, offs, p, c, co)
+    assert as_rows(got) == merge_brute(reads, contigs, p)
