@@ -511,7 +511,8 @@ def run_ours(args):
                            "single_instance": {"value": b["single_instance"]["value"],
                                                "ms_total": round(b["single_instance"]["ms_total"], 2)},
                            "speedup_vs_single_instance": round(b["speedup_vs_single_instance"], 4),
-                           "waves": b["batch_stats"]["waves"], "graph_launches": b["batch_stats"]["graph_launches"]}
+                           "waves": b["batch_stats"]["waves"], "graph_launches": b["batch_stats"]["graph_launches"],
+                           "tuning": b["tuning"]}
         sv = serve_record(EXTRA_SCALE, EXTRA_REQUESTS)
         line["serve"] = {"value": sv["value"], "unit": UNIT, "latency_ms": sv["latency_ms"],
                          "workload": sv["config"]["workload"], "one_at_a_time": sv["one_at_a_time"]["value"],
@@ -615,7 +616,9 @@ def batched_record(scale: float, steps: int, warmup: int, tune: str) -> dict:
                                 "note": "the same jobs, one regular query each, back to back"},
             "speedup_vs_single_instance": t_single / t_batch,
             "tuning": {k: {"keys_per_leaf": round(t.keys_per_leaf, 1), "l1_shift": t.l1_shift,
-                           "distinct_ratio": round(t.distinct_ratio, 4)} for k, t in tunings.items()},
+                           "distinct_ratio": round(t.distinct_ratio, 4), "method": t.method,
+                           "method_ms": t.method_ms, "ms_best": round(t.ms_best, 3),
+                           "ms_default": round(t.ms_default, 3)} for k, t in tunings.items()},
             "setup_s": round(gen_s, 1)}
     b.close()
     for rs in rsets:

@@ -281,6 +281,26 @@ typedef struct {
  * with n > 0, bad where), OOM, CUDA. */
 int kmer_analysis_lookup(kmer_analysis_t *h, const uint64_t *keys, uint64_t n, kmer_record *out, int where);
 
+/* Merge of Algorithm 1 (Merge(k-mer_set, prev_k-mer_set), Sec. II-G): the
+ * survivors of the last query are merged with ExtractKmers(C, k), the k-mers
+ * of a contig set C, which the paper treats as error-free k-mers with unique
+ * high-quality extensions.  A contig k-mer's extension on a side is the
+ * contig's neighbouring base (none at a contig end), in the k-mer's canonical
+ * orientation; over all its occurrences in C a side with one such base is
+ * UNIQUE, with none DEAD_END, with several FORK.  A k-mer found among the
+ * survivors keeps the survivor's record (the two occurrences collapse into
+ * one); a k-mer found only in the contigs is appended after the survivors
+ * with count 0 (no read supports it beyond the count filter), zero tallies
+ * and those classes.  Contigs are given flat like reads (contig i is
+ * contigs[offsets[i] .. offsets[i+1]), any byte other than A, C, G, T breaks
+ * the windows), where = HOST / HOST_STAGED / DEVICE.  *added receives the
+ * number of appended k-mers (may be NULL) and *out the merged view (valid as
+ * a query's view).  Later lookups see the merged set.  Synchronous.  Errors:
+ * INVALID_ARG, BAD_STATE (no successful query, or results written to caller
+ * arrays by kmer_analysis_query_into), OOM, CUDA. */
+int kmer_analysis_merge_contigs(kmer_analysis_t *h, const char *contigs, const uint64_t *offsets, uint64_t n_contigs,
+                                int where, uint64_t *added, kmer_result_view *out);
+
 /* Counters of the last query. */
 int kmer_analysis_get_stats(const kmer_analysis_t *h, kmer_analysis_stats *out);
 

@@ -127,6 +127,8 @@ _SIGNATURES = {
     "kmer_analysis_copy_results": (_int, [_vp, _vp, _vp, _vp, _vp, _u64]),
     "kmer_analysis_lookup": (_int, [_vp, _vp, _u64, _vp, _int]),
     "kmer_analysis_query_into": (_int, [_vp, _vp, _vp, _vp, _vp, _u64, _int, ctypes.POINTER(kmer_result_view)]),
+    "kmer_analysis_merge_contigs": (_int, [_vp, _vp, _vp, _u64, _int, ctypes.POINTER(_u64),
+                                           ctypes.POINTER(kmer_result_view)]),
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
@@ -250,6 +252,15 @@ def kmer_analysis_query_into(h: int, keys: int, count: int, ext: int, cls: int, 
     _check(load_library().kmer_analysis_query_into(h, keys, count, ext, cls, capacity, where, ctypes.byref(v)),
            "kmer_analysis_query_into")
     return v
+
+
+def kmer_analysis_merge_contigs(h: int, contigs: int, offsets: int, n_contigs: int, where: int):
+    """Merge the last query's survivors with the contigs' k-mers; returns (added, view)."""
+    added = _u64()
+    v = kmer_result_view()
+    _check(load_library().kmer_analysis_merge_contigs(h, contigs, offsets, n_contigs, where, ctypes.byref(added),
+                                                      ctypes.byref(v)), "kmer_analysis_merge_contigs")
+    return added.value, v
 
 
 def kmer_analysis_lookup(h: int, keys: int, n: int, out: int, where: int) -> None:
@@ -497,6 +508,18 @@ class KmerAnalysis:
         cls = np.empty((n, 2), dtype=np.uint8)
         kmer_analysis_copy_results(self.handle, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
         return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def merge_contigs(self, contigs, offsets) -> Result:
+        """Merge (Algorithm 1) of the last query's survivors with the k-mers of
+        contigs given flat (bytes or uint8 array, offsets); returns the merged set."""
+        where = _where(contigs)
+        c = contigs if where == KMER_DEVICE else np.ascontiguousarray(np.frombuffer(bytes(contigs), np.uint8)
+                                                                      if isinstance(contigs, (bytes, bytearray))
+                                                                      else contigs, dtype=np.uint8)
+        o = offsets if where == KMER_DEVICE else np.ascontiguousarray(offsets, dtype=np.uint64)
+        n = len(o) - 1
+        _, v = kmer_analysis_merge_contigs(self.handle, _ptr(c) if n else 0, _ptr(o), n, where)
+        return self.results(v)
 
     def lookup(self, keys) -> np.ndarray:
         """Records (KMER_RECORD_DTYPE) of k-mers given as an (n, W) uint64 array,

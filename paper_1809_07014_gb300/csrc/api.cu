@@ -108,7 +108,7 @@ void pinned_misc_put(Misc* m) {
 }
 
 Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
-                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves) {
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves, double l1_slack) {
     Geometry g{};
     g.k = k;
     g.W = (2 * k + 63) / 64;
@@ -129,7 +129,7 @@ Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long lon
     unsigned ps = 0;
     for (;;) {
         const double win = (double)windows / (double)(1ull << ps);
-        const double bytes = win * rec_bytes * (waves ? 1.02 + 2.1 / kMaxWaves : 3.5) +
+        const double bytes = win * rec_bytes * (waves ? 1.0 + l1_slack + 2.1 / kMaxWaves : 3.5) +
                              64.0 * (double)(1ull << (p > ps ? p - ps : 0)) * 8;
         if (bytes <= (waves ? 0.9 : 0.8) * (double)budget || ps >= p || ps >= 12) break;
         ++ps;
@@ -200,6 +200,9 @@ struct kmer_analysis {
     // Bloom gate: filter words (log2), and first sightings / windows at hist_k
     unsigned gate_bits = 0;
     double gate_ratio = 0.0;
+    // level-1 buckets: largest fill / mean fill of the last large query at l1_imb_k
+    unsigned l1_imb_k = 0;
+    double l1_imbalance = 0.0;
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -407,6 +410,15 @@ struct Plan {
     size_t budget;               // device bytes for the records of a pass
 };
 
+// Level-1 slack: an eighth of a bucket's mean, or, after a large query at the
+// same k, a quarter more than the largest bucket's excess over the mean then
+// (repeated k-mers make bucket sizes vary far more than a uniform spread).
+double l1_slack(const kmer_analysis* h) {
+    if (h->l1_imb_k == h->p.k && h->l1_imbalance > 0.0)
+        return std::min(0.25, std::max(0.02, (h->l1_imbalance - 1.0) * 1.25 + 0.01));
+    return 0.125;
+}
+
 Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget, unsigned cap_max,
                unsigned long long gated_distinct = 0) {
     Plan pl{};
@@ -416,7 +428,7 @@ Plan make_plan(const kmer_analysis* h, unsigned long long windows, size_t budget
     else if (h->p.distinct_hint) basis = std::min<unsigned long long>(h->p.distinct_hint, windows);
     else if (h->hist_k == h->p.k && h->hist_ratio > 0.0)  // learned from the previous query at this k
         basis = std::min<unsigned long long>(windows, (unsigned long long)(1.15 * h->hist_ratio * (double)windows) + 1);
-    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, h->p.l1_bits, true);
+    pl.g = plan_geometry(h->p.k, windows, basis, budget, cap_max, h->p.leaf_bits, h->p.l1_bits, true, l1_slack(h));
     pl.passes = 1u << pl.g.ps;
     pl.budget = budget;
     return pl;
@@ -456,6 +468,14 @@ int ensure_output(kmer_analysis* h, unsigned long long cap, unsigned long long k
     ncl.release();
     h->out_cap = cap;
     return KMER_OK;
+}
+
+// The results live in the analysis's own output buffers (after they may have moved).
+void fill_job_outputs_ptrs(kmer_analysis* h) {
+    h->res_keys = h->out_keys.as<unsigned long long>();
+    h->res_count = h->out_count.as<unsigned int>();
+    h->res_ext = h->out_ext.as<unsigned int>();
+    h->res_cls = h->out_cls.as<unsigned char>();
 }
 
 void fill_job_outputs(kmer_analysis* h, Job& j) {
@@ -621,7 +641,7 @@ int run_level2(kmer_analysis* h, Job j, unsigned b0, unsigned nb, unsigned long 
     j.l1_fill += b0;
     std::vector<unsigned long long> exact_leaf;  // exact level-2 layout after an overflow
     if (g.p2) {
-        TRY(h->l2_rec.ensure(l2_capacity * 8 * W + 64));
+        TRY(h->l2_rec.fit(l2_capacity * 8 * W + 64));
         TRY(h->l2_base.ensure(nb * 8ull));
         TRY(h->l2_leafcap.ensure(nb * 4ull));
         TRY(h->l2_fill.ensure(Pw * 8ull));
@@ -717,11 +737,10 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
     const unsigned W = g.W;
     const unsigned long long pass_windows = (pl.windows + pl.passes - 1) / pl.passes;
     std::vector<unsigned long long> caps(P1), starts(P1 + 1);
+    const unsigned long long mean = (pass_windows + P1 - 1) / P1;
     {
-        // the mixed key spreads records evenly: four standard deviations of
-        // slack (a bucket that still overflows is re-scattered with exact sizes)
-        const unsigned long long mean = (pass_windows + P1 - 1) / P1;
-        const unsigned long long slack = 4 * (unsigned long long)std::sqrt((double)mean) + 1024;
+        // a bucket that still overflows is re-scattered with exact sizes
+        const unsigned long long slack = (unsigned long long)(l1_slack(h) * (double)mean) + 1024;
         for (unsigned b = 0; b < P1; ++b) caps[b] = mean + slack;
     }
     const unsigned long long out_start = h->n_out;
@@ -731,7 +750,8 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         starts[0] = 0;
         for (unsigned b = 0; b < P1; ++b) starts[b + 1] = starts[b] + caps[b];
         const unsigned long long l1_total = starts[P1];
-        TRY(h->l1_rec.ensure(l1_total * 8 * W + 64));
+        if (!h->l1_rec.fits(l1_total * 8 * W + 64)) h->l2_rec.release();  // never both old and new at once
+        TRY(h->l1_rec.fit(l1_total * 8 * W + 64));
         // the repartition's bulk copies start on 16-byte boundaries of this region
         if (reinterpret_cast<uintptr_t>(h->l1_rec.p) & 15)
             return fail(KMER_ERR_CUDA, "level-1 record buffer is not 16-byte aligned");
@@ -838,6 +858,16 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         }
         if (tot.windows != tot.emitted)  // every emitted window must be counted by exactly one leaf
             return fail(KMER_ERR_CUDA, "internal: %llu windows emitted but %llu counted", tot.emitted, tot.windows);
+        if (pass_windows >= (1ull << 26)) {  // learn the buckets' imbalance for the next large query
+            std::vector<unsigned long long> fill(P1);
+            CK(cudaMemcpyAsync(fill.data(), h->l1_fill.p, P1 * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            const double em = (double)tot.emitted / (double)P1;
+            if (em > 0) {
+                h->l1_imbalance = (double)*std::max_element(fill.begin(), fill.end()) / em;
+                h->l1_imb_k = h->p.k;
+            }
+        }
         h->n_out = tot.out_n;
         h->res_windows += tot.windows;
         h->res_distinct += tot.distinct;
@@ -859,8 +889,8 @@ int run_gate(kmer_analysis* h, unsigned long long windows, unsigned long long (&
     while ((1ull << bits) * 64 < keys * 8 && bits < 40) ++bits;
     h->gate_bits = bits;
     const size_t bytes = (size_t)8 << bits;
-    TRY(h->gate1.ensure(bytes));
-    TRY(h->gate2.ensure(bytes));
+    TRY(h->gate1.fit(bytes));
+    TRY(h->gate2.fit(bytes));
     TRY(h->gate_cnt.ensure(3 * 8));
     CK(cudaMemsetAsync(h->gate1.p, 0, bytes, h->stream));
     CK(cudaMemsetAsync(h->gate2.p, 0, bytes, h->stream));
@@ -1290,6 +1320,93 @@ int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, k
     if (where == KMER_HOST)
         CK(cudaMemcpyAsync(out, dout, n * sizeof(kmer_record), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return KMER_OK;
+}
+
+int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const uint64_t* offsets,
+                                uint64_t n_contigs, int where, uint64_t* added, kmer_result_view* out) {
+    if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
+    if (!valid_where(where)) return fail(KMER_ERR_INVALID_ARG, "where must be HOST, DEVICE or HOST_STAGED");
+    if (n_contigs && (!contigs || !offsets)) return fail(KMER_ERR_INVALID_ARG, "NULL contigs with n_contigs > 0");
+    if (!h->have_result) return fail(KMER_ERR_BAD_STATE, "no successful query to merge into");
+    if (h->res_keys != h->out_keys.as<unsigned long long>())
+        return fail(KMER_ERR_BAD_STATE, "the results are in the caller's arrays (query_into): query again first");
+    DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
+    std::memset(out, 0, sizeof *out);
+    if (added) *added = 0;
+    const unsigned W = h->W();
+    if (n_contigs) {
+        if (h->n_out >= 0xFFFFFFFFull) return fail(KMER_ERR_INVALID_ARG, "index limited to 2^32 - 2 survivors");
+        // ExtractKmers: the contigs' k-mers as a k-mer analysis of the contigs
+        // with every base of high quality (the bases serve as their own quality
+        // bytes, offset 0, threshold 0), no count filter, and classes by the
+        // static rule with t_ext = 1: a side is UNIQUE when one base follows it
+        // anywhere in the contigs, DEAD_END when none, FORK when several
+        kmer_readset_t* crs = nullptr;
+        TRY(make_readset(contigs, reinterpret_cast<const uint8_t*>(contigs), offsets, n_contigs, 0, 0, where,
+                         h->stream, &crs));
+        kmer_analysis_params cp;
+        kmer_analysis_default_params(&cp, h->p.k);
+        cp.min_count = 1;
+        cp.qual_offset = 0;
+        cp.qual_threshold = 0;
+        cp.ext_mode = KMER_EXT_STATIC;
+        cp.t_ext = 1;
+        kmer_analysis_t* b = nullptr;
+        int rc = kmer_analysis_create(&cp, h->stream, &b);
+        kmer_result_view bv{};
+        if (rc == KMER_OK) rc = kmer_analysis_submit(b, crs);
+        if (rc == KMER_OK) rc = kmer_analysis_query(b, &bv);
+        if (rc == KMER_OK && !h->lk_cap) {  // index of the current survivors
+            const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * h->n_out));
+            rc = h->lk_index.ensure(cap * 4);
+            if (rc == KMER_OK && (cudaMemsetAsync(h->lk_index.p, 0xFF, cap * 4, h->stream) != cudaSuccess ||
+                                  launch_index_build(W, h->res_keys, h->n_out, h->lk_index.as<unsigned>(), cap,
+                                                     h->num_sms, h->stream) != cudaSuccess))
+                rc = fail(KMER_ERR_CUDA, "building the survivors' index failed");
+            if (rc == KMER_OK) h->lk_cap = cap;
+        }
+        const unsigned long long n0 = h->n_out;
+        if (rc == KMER_OK) rc = ensure_output(h, n0 + bv.n, n0);
+        if (rc == KMER_OK) {
+            fill_job_outputs_ptrs(h);
+            rc = reset_misc(h, n0);
+        }
+        if (rc == KMER_OK) {
+            Misc* m = h->misc.as<Misc>();
+            if (launch_merge_append(W, reinterpret_cast<const unsigned long long*>(bv.keys), bv.cls, bv.n,
+                                    h->lk_index.as<unsigned>(), h->lk_cap, h->res_keys, h->res_count, h->res_ext,
+                                    h->res_cls, h->out_cap, &m->out_n, &m->status, h->num_sms,
+                                    h->stream) != cudaSuccess)
+                rc = fail(KMER_ERR_CUDA, "merge kernel launch failed");
+            h->st.launches++;
+        }
+        if (rc == KMER_OK) rc = read_misc(h);
+        if (rc == KMER_OK && h->host_misc->status)
+            rc = fail(KMER_ERR_CUDA, "internal: merged k-mers past the output capacity");
+        if (rc == KMER_OK) {
+            h->n_out = h->host_misc->out_n;
+            h->lk_cap = 0;  // the index does not cover the added k-mers
+            if (added) *added = h->n_out - n0;
+        }
+        if (b) kmer_analysis_destroy(b);
+        kmer_readset_destroy(crs);
+        if (rc != KMER_OK) {
+            h->have_result = false;
+            cudaGetLastError();
+            return rc;
+        }
+    }
+    out->n = h->n_out;
+    out->k = h->p.k;
+    out->words = W;
+    out->keys = reinterpret_cast<const uint64_t*>(h->res_keys);
+    out->count = h->res_count;
+    out->ext = h->res_ext;
+    out->cls = h->res_cls;
+    out->windows = h->res_windows;
+    out->distinct = h->res_distinct;
     return KMER_OK;
 }
 

@@ -94,6 +94,15 @@ struct DevBuf {
         bytes = n;
         return KMER_OK;
     }
+    // Holds n bytes without wasting more than a quarter (plus 64 MB): grows, or
+    // shrinks a buffer much larger than needed (device memory held across
+    // queries counts against the next query's budget).
+    bool fits(size_t n) const { return p && n <= bytes && bytes <= n + n / 4 + (64ull << 20); }
+    int fit(size_t n) {
+        if (fits(n)) return KMER_OK;
+        release();
+        return ensure(n);
+    }
     void release() {
         if (p) cudaFreeAsync(p, s);
         p = nullptr;
@@ -140,7 +149,7 @@ void analysis_set_sizing(kmer_analysis_t* h, uint64_t memory_budget, uint64_t di
 // held at a time.
 constexpr unsigned kMaxWaves = 8;
 Geometry plan_geometry(unsigned k, unsigned long long windows, unsigned long long basis, size_t budget,
-                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves);
+                       unsigned cap_max, unsigned leaf_bits, unsigned l1_bits, bool waves, double l1_slack = 0.125);
 
 }  // namespace kmer
 

@@ -43,6 +43,16 @@ cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsig
 cudaError_t launch_gate(const Job& j, unsigned long long* f1, unsigned long long* f2, unsigned log2_words,
                         unsigned long long* counts, cudaStream_t s);
 
+// Merge (Algorithm 1): k-mers of a second canonical, distinct set (bkeys,
+// bcls; bn of them) absent from the indexed survivors are appended to them
+// from position *n_out on (count 0, zero tallies, their own classes); a
+// position past out_cap sets bit 0 of *status.
+cudaError_t launch_merge_append(unsigned W, const unsigned long long* bkeys, const unsigned char* bcls,
+                                unsigned long long bn, const unsigned* idx, unsigned long long cap,
+                                unsigned long long* keys, unsigned* count, unsigned* ext, unsigned char* cls,
+                                unsigned long long out_cap, unsigned long long* n_out, unsigned* status, int num_sms,
+                                cudaStream_t s);
+
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
 // tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles; min_k =
 // the smallest k of the jobs (one-word keys with k >= 17 roll on their high

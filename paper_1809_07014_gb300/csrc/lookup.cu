@@ -111,6 +111,68 @@ __global__ void __launch_bounds__(256) lookup_kernel(const unsigned long long* _
     }
 }
 
+// Merge of Algorithm 1 (Sec. II-G): every k-mer of a second set (the
+// contigs' k-mers, canonical and distinct) that is not among the survivors
+// is appended to the survivors with count 0, zero tallies and its own
+// classes; one that is already there keeps the survivor's record (the two
+// occurrences collapse into one).  The index covers the survivors present
+// before the merge; `n_out` counts appended positions (one reservation per
+// warp).
+template <int W>
+__global__ void __launch_bounds__(256) merge_append_kernel(const unsigned long long* __restrict__ bkeys,
+                                                           const unsigned char* __restrict__ bcls,
+                                                           unsigned long long bn, const unsigned* __restrict__ idx,
+                                                           unsigned long long cap, unsigned long long* keys,
+                                                           unsigned* count, unsigned* ext, unsigned char* cls,
+                                                           unsigned long long out_cap,
+                                                           unsigned long long* __restrict__ n_out,
+                                                           unsigned* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * 256;
+    for (unsigned long long base = blockIdx.x * 256ull + (threadIdx.x & ~31u); base < bn; base += stride) {
+        const unsigned long long i = base + lane;
+        bool add = false;
+        unsigned long long key[W];
+        if (i < bn) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) key[w] = bkeys[i * W + w];
+            add = true;
+            unsigned long long s = key_hash<W>(key) & (cap - 1);
+            for (unsigned long long probe = 0; probe < cap; ++probe) {
+                const unsigned p = idx[s];
+                if (p == kIdxEmpty) break;
+                bool same = true;
+#pragma unroll
+                for (int w = 0; w < W; ++w) same = same && keys[(unsigned long long)p * W + w] == key[w];
+                if (same) {
+                    add = false;
+                    break;
+                }
+                s = (s + 1) & (cap - 1);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, add);
+        unsigned long long first = 0;
+        if (lane == 0 && m) first = atomicAdd(n_out, (unsigned long long)__popc(m));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (add) {
+            const unsigned long long pos = first + __popc(m & ((1u << lane) - 1u));
+            if (pos >= out_cap) {
+                atomicOr(status, 1u);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) keys[pos * W + w] = key[w];
+                count[pos] = 0;
+                uint4* eo = reinterpret_cast<uint4*>(ext + pos * 8);
+                eo[0] = make_uint4(0, 0, 0, 0);
+                eo[1] = make_uint4(0, 0, 0, 0);
+                cls[2 * pos] = bcls[2 * i];
+                cls[2 * pos + 1] = bcls[2 * i + 1];
+            }
+        }
+    }
+}
+
 static unsigned grid_of(unsigned long long n, int num_sms) {
     unsigned long long g = (n + 255) / 256, cap = (unsigned long long)num_sms * 8;
     if (g > cap) g = cap;
@@ -126,6 +188,23 @@ cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsig
         case 2: index_build_kernel<2><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
         case 3: index_build_kernel<3><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
         case 4: index_build_kernel<4><<<g, 256, 0, s>>>(keys, n, idx, cap); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_append(unsigned W, const unsigned long long* bkeys, const unsigned char* bcls,
+                                unsigned long long bn, const unsigned* idx, unsigned long long cap,
+                                unsigned long long* keys, unsigned* count, unsigned* ext, unsigned char* cls,
+                                unsigned long long out_cap, unsigned long long* n_out, unsigned* status, int num_sms,
+                                cudaStream_t s) {
+    if (bn == 0) return cudaSuccess;
+    const unsigned g = grid_of(bn, num_sms);
+    switch (W) {
+        case 1: merge_append_kernel<1><<<g, 256, 0, s>>>(bkeys, bcls, bn, idx, cap, keys, count, ext, cls, out_cap, n_out, status); break;
+        case 2: merge_append_kernel<2><<<g, 256, 0, s>>>(bkeys, bcls, bn, idx, cap, keys, count, ext, cls, out_cap, n_out, status); break;
+        case 3: merge_append_kernel<3><<<g, 256, 0, s>>>(bkeys, bcls, bn, idx, cap, keys, count, ext, cls, out_cap, n_out, status); break;
+        case 4: merge_append_kernel<4><<<g, 256, 0, s>>>(bkeys, bcls, bn, idx, cap, keys, count, ext, cls, out_cap, n_out, status); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
