@@ -74,6 +74,12 @@ def _load():
             lib.oracle_merge_contigs.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(_Params), vp, vp,
                                                  ctypes.c_uint64, ctypes.POINTER(_Result)]
             lib.oracle_merge_contigs.restype = ctypes.c_int
+            lib.oracle_traverse.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_traverse.restype = ctypes.c_int
+            lib.oracle_free_contigs.argtypes = [vp, vp]
+            lib.oracle_free_contigs.restype = None
             lib.oracle_free.argtypes = [ctypes.POINTER(_Result)]
             lib.oracle_free.restype = None
             lib.oracle_fnv1a.argtypes = [ctypes.c_char_p, ctypes.c_uint64]
@@ -206,6 +212,29 @@ def merge_contigs(bases, quals, offsets, params: Params, contigs, contig_offsets
                                   ctypes.c_void_p(c.ctypes.data if len(c) else 0), ctypes.c_void_p(co.ctypes.data),
                                   n_contigs, ctypes.byref(res))
     return _collect(lib, res, rc, params.k)
+
+
+def traverse(keys: np.ndarray, cls: np.ndarray) -> list[bytes]:
+    """De Bruijn graph traversal (Sec. II-C) over a k-mer set (keys: S{k}
+    strings, cls: (n, 2) classes): the contigs, each the smaller of itself and
+    its reverse complement, in ascending order (see kmer_oracle.cpp)."""
+    lib = _load()
+    keys = np.ascontiguousarray(keys)
+    k = keys.dtype.itemsize
+    cls = np.ascontiguousarray(cls, dtype=np.uint8)
+    n = len(keys)
+    c_ptr, o_ptr, nc = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint64()
+    rc = lib.oracle_traverse(ctypes.c_void_p(keys.ctypes.data if n else 0), ctypes.c_void_p(cls.ctypes.data if n else 0),
+                             n, k, ctypes.byref(c_ptr), ctypes.byref(o_ptr), ctypes.byref(nc))
+    if rc:
+        raise ValueError(f"oracle_traverse rejected its arguments (status {rc})")
+    try:
+        m = int(nc.value)
+        offs = np.frombuffer(ctypes.string_at(o_ptr, 8 * (m + 1)), dtype=np.uint64)
+        data = ctypes.string_at(c_ptr, int(offs[-1])) if m else b""
+        return [data[int(offs[i]):int(offs[i + 1])] for i in range(m)]
+    finally:
+        lib.oracle_free_contigs(c_ptr, o_ptr)
 
 
 def host_threads() -> int:

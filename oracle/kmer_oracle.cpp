@@ -40,6 +40,7 @@
  * tallies are sums over windows, and update-only inserts commute
  * (Sec. II-A, use case 1).
  */
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -405,6 +406,112 @@ extern "C" int oracle_merge_contigs(const char *bases, const uint8_t *quals, con
     }
     oracle_free(&reads);
     return 0;
+}
+
+/* De Bruijn graph traversal (Sec. II-C): contigs are the paths formed by
+ * k-mers with unique extensions.  Reading taken here:
+ *  - a vertex is a k-mer of the set whose two sides are both UNIQUE (classes
+ *    0..3); a k-mer x read in either orientation has, in that orientation, a
+ *    left base l(x) and a right base r(x) (for the reverse complement of a
+ *    stored k-mer: the complements of its right and left classes);
+ *  - x and y = x[1..k) + r(x) are joined when y's canonical form is a vertex
+ *    other than x's and l(y) = x[0] (each names the other); a k-mer followed
+ *    by its own reverse complement (a hairpin) is joined to nothing there, so
+ *    that every contig uses a k-mer at most once;
+ *  - a contig is a maximal path: its first k-mer, then the right base of every
+ *    later k-mer; a cycle is cut before its smallest canonical k-mer and read
+ *    from that k-mer in its stored orientation;
+ *  - each contig is reported as the smaller of its string and its reverse
+ *    complement, and the contigs in ascending order.
+ * The contigs are written to *contigs (malloc'd, concatenated) with
+ * *offsets (n_contigs + 1 entries, malloc'd). */
+extern "C" int oracle_traverse(const char *keys, const uint8_t *cls, uint64_t n, uint32_t k, char **contigs,
+                               uint64_t **offsets, uint64_t *n_contigs) {
+    if ((n && (!keys || !cls)) || !contigs || !offsets || !n_contigs || k == 0) return -1;
+    std::map<std::string, std::pair<int, int>> vert;  // canonical k-mer -> (left, right) of its stored orientation
+    for (uint64_t i = 0; i < n; ++i)
+        if (cls[2 * i] < 4 && cls[2 * i + 1] < 4) vert[std::string(keys + i * k, keys + (i + 1) * k)] = {cls[2 * i], cls[2 * i + 1]};
+    const char *base = "ACGT";
+    auto canon = [](const std::string &x) {
+        const std::string r = reverse_complement(x);
+        return r < x ? r : x;
+    };
+    // left and right base of x in its own orientation, or false if x is no vertex
+    auto sides = [&](const std::string &x, int &l, int &r) {
+        const std::string c = canon(x);
+        auto it = vert.find(c);
+        if (it == vert.end()) return false;
+        if (c == x) {
+            l = it->second.first;
+            r = it->second.second;
+        } else {
+            l = 3 - it->second.second;
+            r = 3 - it->second.first;
+        }
+        return true;
+    };
+    auto next = [&](const std::string &x, std::string &y) {  // the vertex joined to x's right, if any
+        int l, r, l2, r2;
+        if (!sides(x, l, r)) return false;
+        y = x.substr(1) + base[r];
+        return canon(y) != canon(x) && sides(y, l2, r2) && base[l2] == x[0];
+    };
+    auto prev = [&](const std::string &x, std::string &y) {  // the vertex joined to x's left, if any
+        int l, r, l2, r2;
+        if (!sides(x, l, r)) return false;
+        y = std::string(1, base[l]) + x.substr(0, x.size() - 1);
+        return canon(y) != canon(x) && sides(y, l2, r2) && base[r2] == x[x.size() - 1];
+    };
+    std::set<std::string> used;
+    std::vector<std::string> out;
+    for (const auto &kv : vert) {
+        if (used.count(kv.first)) continue;
+        // walk left to the path's start, or around a cycle back to this k-mer
+        std::string x = kv.first, y;
+        bool cycle = false;
+        while (prev(x, y)) {
+            if (canon(y) == kv.first) {
+                cycle = true;
+                break;
+            }
+            x = y;
+        }
+        if (cycle) {  // start at the cycle's smallest canonical k-mer, stored orientation
+            std::string m = kv.first, z = kv.first;
+            while (next(z, y) && canon(y) != kv.first) {
+                z = y;
+                if (canon(z) < m) m = canon(z);
+            }
+            x = m;
+        }
+        std::string contig = x;
+        used.insert(canon(x));
+        while (next(x, y) && !used.count(canon(y))) {
+            contig += y.back();
+            used.insert(canon(y));
+            x = y;
+        }
+        const std::string rc = reverse_complement(contig);
+        out.push_back(rc < contig ? rc : contig);
+    }
+    std::sort(out.begin(), out.end());
+    uint64_t total = 0;
+    for (const auto &c : out) total += c.size();
+    *contigs = (char *)std::malloc(total + 1);
+    *offsets = (uint64_t *)std::malloc(sizeof(uint64_t) * (out.size() + 1));
+    if (!*contigs || !*offsets) return -2;
+    (*offsets)[0] = 0;
+    for (size_t i = 0; i < out.size(); ++i) {
+        std::memcpy(*contigs + (*offsets)[i], out[i].data(), out[i].size());
+        (*offsets)[i + 1] = (*offsets)[i] + out[i].size();
+    }
+    *n_contigs = out.size();
+    return 0;
+}
+
+extern "C" void oracle_free_contigs(char *contigs, uint64_t *offsets) {
+    std::free(contigs);
+    std::free(offsets);
 }
 
 extern "C" void oracle_free(oracle_result *r) {

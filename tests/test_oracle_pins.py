@@ -492,3 +492,145 @@ def test_merge_against_brute_force(seed):
     c, co = flat(contigs)
     got = oracle.merge_contigs(bases, quals, offs, p, c, co)
     assert as_rows(got) == merge_brute(reads, contigs, p)
+
+
+# ------------------------------------------------------ de Bruijn graph traversal
+def rc_str(s):
+    return "".join(COMP[c] for c in reversed(s))
+
+
+def traverse_brute(keys, cls):
+    """Sec. II-C written differently: each canonical k-mer with two UNIQUE
+    sides has two ports (left, right); an oriented k-mer x links its right
+    port to y = x[1..] + r(x) when y is another such k-mer naming x back
+    (hairpins, x followed by its own reverse complement, link nothing).
+    Components are chains or rings of ports; a chain is read from an end, a
+    ring from its smallest k-mer in stored orientation."""
+    keys = [x.decode() if isinstance(x, bytes) else x for x in keys]
+    uu = {key: (int(c[0]), int(c[1])) for key, c in zip(keys, cls) if c[0] < 4 and c[1] < 4}
+
+    def lr(x):
+        c = min(x, rc_str(x))
+        if c not in uu:
+            return None
+        l, r = uu[c]
+        return (l, r) if c == x else (3 - r, 3 - l)
+
+    def right(x):  # the oriented k-mer joined to x's right, or None
+        s = lr(x)
+        if s is None:
+            return None
+        y = x[1:] + ORDER[s[1]]
+        t = lr(y)
+        if t is None or ORDER[t[0]] != x[0] or min(y, rc_str(y)) == min(x, rc_str(x)):
+            return None
+        return y
+
+    # port of oriented x's right side: (canonical, 1) if x is stored, else (canonical, 0)
+    def rport(x):
+        c = min(x, rc_str(x))
+        return (c, 1 if c == x else 0)
+
+    link = {}
+    for c in uu:
+        for x in (c, rc_str(c)):
+            y = right(x)
+            if y is not None:
+                a, b = rport(x), rport(rc_str(y))  # y's left side is the right side of rc(y)
+                link[a], link[b] = b, a
+    out, seen = [], set()
+    for c in sorted(uu):
+        if c in seen:
+            continue
+        # walk out of the left port to the end of the chain (or once around a ring)
+        v, p, ring = c, 0, False
+        while (v, p) in link:
+            v, q = link[(v, p)]
+            p = 1 - q
+            if v == c:
+                ring = True
+                break
+        if ring:
+            ring_members, v, p = [c], c, 1
+            while True:
+                v, q = link[(v, p)]
+                p = 1 - q
+                if v == c:
+                    break
+                ring_members.append(v)
+            start, port = min(ring_members), 1
+        else:
+            start, port = v, 1 - p  # the end reached, leaving through its other port
+        x = start if port == 1 else rc_str(start)
+        s, v, p = x, start, port
+        seen.add(start)
+        while (v, p) in link:
+            w, q = link[(v, p)]
+            if w in seen:
+                break
+            seen.add(w)
+            # w is read in stored orientation when entered through its left port
+            y = w if q == 0 else rc_str(w)
+            s += y[-1]
+            v, p = w, 1 - q
+        out.append(min(s, rc_str(s)))
+    return sorted(out)
+
+
+def genome_reads(g, L, step):
+    return [(g[i:i + L], b"I" * L) for i in range(0, len(g) - L + 1, step)]
+
+
+def test_traversal_of_one_genome_is_one_contig():
+    """Error-free tiled reads of a sequence with no repeated 7-mer: every inner
+    k-mer has unique extensions; the first and last k-mers have a dead end, so
+    the contig is the genome without its first and last base."""
+    g = b"ACGTTGCATGCCATAGGCTTACAGGATCCATTGACGGTACAT"
+    res = oracle.run_reads(genome_reads(g, 20, 2), oracle.Params(k=7, min_count=1))
+    want = g[1:-1]
+    want = min(want, want.translate(bytes.maketrans(b"ACGT", b"TGCA"))[::-1])
+    assert oracle.traverse(res.keys, res.cls) == [want]
+
+
+def test_traversal_is_strand_symmetric():
+    g = b"ACGTTGCATGCCATAGGCTTACAGGATCCATTGACGGTACAT"
+    fwd = oracle.run_reads(genome_reads(g, 20, 2), oracle.Params(k=7, min_count=1))
+    rcg = g.translate(bytes.maketrans(b"ACGT", b"TGCA"))[::-1]
+    rev = oracle.run_reads(genome_reads(rcg, 20, 2), oracle.Params(k=7, min_count=1))
+    assert oracle.traverse(fwd.keys, fwd.cls) == oracle.traverse(rev.keys, rev.cls)
+
+
+def test_traversal_of_a_tandem_repeat_is_a_cycle():
+    """Reads of a long period-7 repeat (no 5-mer equals another's reverse
+    complement): seven k-mers in a ring; the contig is read from the smallest
+    of them in stored orientation, one period plus k - 1 bases."""
+    g = b"ACCGTTG" * 14
+    res = oracle.run_reads(genome_reads(g, 40, 1), oracle.Params(k=5, min_count=1))
+    got = oracle.traverse(res.keys, res.cls)
+    assert len(res) == 7 and len(got) == 1 and len(got[0]) == 7 + 5 - 1
+    assert got == [x.encode() for x in traverse_brute(res.keys, res.cls)]
+
+
+def test_traversal_of_a_palindromic_repeat_uses_each_kmer_once():
+    """A repeat whose reverse complement is a rotation of itself: a k-mer is
+    followed by its own reverse complement (a hairpin), which joins nothing;
+    every k-mer appears in exactly one contig."""
+    g = b"ACGTTGCA" * 12
+    res = oracle.run_reads(genome_reads(g, 40, 1), oracle.Params(k=5, min_count=1))
+    got = oracle.traverse(res.keys, res.cls)
+    assert got == [x.encode() for x in traverse_brute(res.keys, res.cls)]
+    assert sum(len(c) - 5 + 1 for c in got) == len(res)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_traversal_against_brute_force(seed):
+    rng = random.Random(5000 + seed)
+    k = rng.choice([3, 5, 7])
+    # k-mer sets from a few random sequences read as tiled reads, plus random noise k-mers
+    seqs = ["".join(rng.choice(ORDER) for _ in range(rng.randint(k + 2, 60))) for _ in range(rng.randint(1, 4))]
+    reads = [(s.encode()[i:i + 15], b"I" * 15) for s in seqs for i in range(0, max(1, len(s) - 14), 3)]
+    reads += random_reads(rng, rng.randint(0, 5), k, 20)
+    res = oracle.run_reads(reads, oracle.Params(k=k, min_count=1, ext_mode=rng.choice([0, 1])))
+    if len(res) == 0:
+        return
+    assert [c.decode() for c in oracle.traverse(res.keys, res.cls)] == traverse_brute(res.keys, res.cls)
