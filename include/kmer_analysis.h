@@ -301,6 +301,38 @@ int kmer_analysis_lookup(kmer_analysis_t *h, const uint64_t *keys, uint64_t n, k
 int kmer_analysis_merge_contigs(kmer_analysis_t *h, const char *contigs, const uint64_t *offsets, uint64_t n_contigs,
                                 int where, uint64_t *added, kmer_result_view *out);
 
+/* Contigs of a de Bruijn graph traversal (kmer_analysis_traverse): device
+ * pointers owned by the analysis, valid until the next query, merge, reset or
+ * destroy.  Contig i is seq[offsets[i] .. offsets[i+1]) (ASCII A/C/G/T). */
+typedef struct {
+    uint64_t n_contigs;
+    uint64_t bases;             /* offsets[n_contigs] */
+    const char *seq;
+    const uint64_t *offsets;    /* n_contigs + 1 entries */
+} kmer_contigs_view;
+
+/* De Bruijn graph traversal (Sec. II-C, DeBruijnGraphTraversal of Algorithm
+ * 1) over the current k-mer set (the last query's survivors, merged with
+ * contig k-mers if kmer_analysis_merge_contigs ran): contigs are the paths
+ * formed by k-mers with unique extensions.  A vertex is a k-mer whose two
+ * sides are both UNIQUE; a k-mer read in an orientation x and its right
+ * neighbour y = x[1..k) + (x's right base) are joined when y's canonical form
+ * is another vertex whose left base, in y's orientation, is x[0] (each names
+ * the other; a k-mer followed by its own reverse complement is joined to
+ * nothing there).  A contig is a maximal path (its first k-mer, then one base
+ * per later k-mer); a ring is cut before its smallest canonical k-mer.  Each
+ * contig is reported as the smaller of itself and its reverse complement;
+ * the contigs come in no particular order.  Computed by list ranking on the
+ * device.  Synchronous.  Errors: BAD_STATE (no successful query),
+ * INVALID_ARG (more than 2^31 - 1 k-mers), OOM, CUDA. */
+int kmer_analysis_traverse(kmer_analysis_t *h, kmer_contigs_view *out);
+
+/* Copies the contigs of the last traversal to host (or device) memory:
+ * seq (bases), offsets (n_contigs + 1); either may be NULL.  Errors:
+ * BAD_STATE (no traversal since the last query), INVALID_ARG (too small). */
+int kmer_analysis_copy_contigs(kmer_analysis_t *h, char *seq, uint64_t *offsets, uint64_t seq_capacity,
+                               uint64_t contig_capacity);
+
 /* Counters of the last query. */
 int kmer_analysis_get_stats(const kmer_analysis_t *h, kmer_analysis_stats *out);
 

@@ -78,6 +78,11 @@ class kmer_analysis_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class kmer_contigs_view(ctypes.Structure):
+    _fields_ = [("n_contigs", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("seq", ctypes.c_void_p),
+                ("offsets", ctypes.c_void_p)]
+
+
 class kmer_batch_job(ctypes.Structure):
     _fields_ = [("readset", ctypes.c_void_p), ("params", kmer_analysis_params), ("survivors_hint", ctypes.c_uint64)]
 
@@ -129,6 +134,8 @@ _SIGNATURES = {
     "kmer_analysis_query_into": (_int, [_vp, _vp, _vp, _vp, _vp, _u64, _int, ctypes.POINTER(kmer_result_view)]),
     "kmer_analysis_merge_contigs": (_int, [_vp, _vp, _vp, _u64, _int, ctypes.POINTER(_u64),
                                            ctypes.POINTER(kmer_result_view)]),
+    "kmer_analysis_traverse": (_int, [_vp, ctypes.POINTER(kmer_contigs_view)]),
+    "kmer_analysis_copy_contigs": (_int, [_vp, _vp, _vp, _u64, _u64]),
     "kmer_analysis_get_stats": (_int, [_vp, ctypes.POINTER(kmer_analysis_stats)]),
     "kmer_analysis_reset": (_int, [_vp]),
     "kmer_analysis_destroy": (_int, [_vp]),
@@ -261,6 +268,17 @@ def kmer_analysis_merge_contigs(h: int, contigs: int, offsets: int, n_contigs: i
     _check(load_library().kmer_analysis_merge_contigs(h, contigs, offsets, n_contigs, where, ctypes.byref(added),
                                                       ctypes.byref(v)), "kmer_analysis_merge_contigs")
     return added.value, v
+
+
+def kmer_analysis_traverse(h: int) -> kmer_contigs_view:
+    v = kmer_contigs_view()
+    _check(load_library().kmer_analysis_traverse(h, ctypes.byref(v)), "kmer_analysis_traverse")
+    return v
+
+
+def kmer_analysis_copy_contigs(h: int, seq: int, offsets: int, seq_capacity: int, contig_capacity: int) -> None:
+    _check(load_library().kmer_analysis_copy_contigs(h, seq, offsets, seq_capacity, contig_capacity),
+           "kmer_analysis_copy_contigs")
 
 
 def kmer_analysis_lookup(h: int, keys: int, n: int, out: int, where: int) -> None:
@@ -508,6 +526,16 @@ class KmerAnalysis:
         cls = np.empty((n, 2), dtype=np.uint8)
         kmer_analysis_copy_results(self.handle, _ptr(keys), _ptr(count), _ptr(ext), _ptr(cls), n)
         return Result(int(v.k), keys, count, ext, cls, int(v.windows), int(v.distinct))
+
+    def traverse(self) -> list[bytes]:
+        """Contigs of the de Bruijn graph traversal (Sec. II-C) over the current
+        k-mer set, each the smaller of itself and its reverse complement."""
+        v = kmer_analysis_traverse(self.handle)
+        seq = np.empty(max(1, int(v.bases)), dtype=np.uint8)
+        offs = np.empty(int(v.n_contigs) + 1, dtype=np.uint64)
+        kmer_analysis_copy_contigs(self.handle, _ptr(seq), _ptr(offs), int(v.bases), int(v.n_contigs))
+        data = seq.tobytes()
+        return [data[int(offs[i]):int(offs[i + 1])] for i in range(int(v.n_contigs))]
 
     def merge_contigs(self, contigs, offsets) -> Result:
         """Merge (Algorithm 1) of the last query's survivors with the k-mers of

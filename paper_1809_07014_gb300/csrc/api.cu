@@ -171,6 +171,9 @@ struct kmer_analysis {
     DevBuf out_keys, out_count, out_ext, out_cls;
     DevBuf fb_list, split_list, hbm, misc;
     DevBuf gate1, gate2, gate_cnt;  // Bloom gate: filters F1, F2 and the gate pass's counters
+    DevBuf trav_scratch, trav_bases, trav_off, trav_tot;  // graph traversal: scratch and contigs
+    unsigned long long n_contigs = 0, contig_bases = 0;
+    bool have_contigs = false;
     DevBuf lk_index, lk_keys, lk_out;  // survivors' index for lookups, staging of host lookups
     // survivors written straight into caller buffers (kmer_analysis_query_into): device
     // addresses of those buffers while such a query runs, and of the results after it
@@ -211,7 +214,8 @@ struct kmer_analysis {
                               &l2_leaf_start, &tile_prefix, &out_keys, &out_count, &out_ext, &out_cls,
                               &fb_list, &split_list, &hbm, &misc, &lk_index, &lk_keys, &lk_out, &d_ajob,
                               &d_sjobs, &d_tile_off, &d_leaf_off,
-                              &d_job_tile_off, &gate1, &gate2, &gate_cnt};
+                              &d_job_tile_off, &gate1, &gate2, &gate_cnt, &trav_scratch, &trav_bases, &trav_off,
+                              &trav_tot};
         size_t t = 0;
         for (auto* b : bs) t += b->bytes;
         return t;
@@ -968,6 +972,7 @@ int run_direct(kmer_analysis* h, unsigned long long windows) {
 int do_query(kmer_analysis* h) {
     const auto t0 = std::chrono::steady_clock::now();
     h->have_result = false;
+    h->have_contigs = false;
     h->lk_cap = 0;
     h->n_out = h->res_windows = h->res_distinct = 0;
     const kmer_analysis_stats zero{};
@@ -1323,6 +1328,66 @@ int kmer_analysis_lookup(kmer_analysis_t* h, const uint64_t* keys, uint64_t n, k
     return KMER_OK;
 }
 
+// The survivors' index for lookups, merges and traversals (built once per result).
+int ensure_index(kmer_analysis* h) {
+    if (h->lk_cap) return KMER_OK;
+    const unsigned long long cap = next_pow2(std::max<unsigned long long>(1024, 2 * h->n_out));
+    TRY(h->lk_index.ensure(cap * 4));
+    CK(cudaMemsetAsync(h->lk_index.p, 0xFF, cap * 4, h->stream));
+    CK(launch_index_build(h->W(), h->res_keys, h->n_out, h->lk_index.as<unsigned>(), cap, h->num_sms, h->stream));
+    h->lk_cap = cap;
+    return KMER_OK;
+}
+
+int kmer_analysis_traverse(kmer_analysis_t* h, kmer_contigs_view* out) {
+    if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
+    if (!h->have_result) return fail(KMER_ERR_BAD_STATE, "no successful query to traverse");
+    if (h->n_out > 0x7FFFFFFFull) return fail(KMER_ERR_INVALID_ARG, "traversal limited to 2^31 - 1 k-mers");
+    DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
+    std::memset(out, 0, sizeof *out);
+    const unsigned W = h->W();
+    const unsigned long long n = h->n_out;
+    TRY(ensure_index(h));
+    TRY(h->trav_scratch.fit(traverse_scratch_bytes(n)));
+    TRY(h->trav_tot.ensure(16));
+    CK(launch_traverse_plan(W, h->res_keys, h->res_cls, n, h->p.k, h->lk_index.as<unsigned>(), h->lk_cap,
+                            h->trav_scratch.p, h->trav_tot.as<unsigned long long>(), h->num_sms, h->stream));
+    unsigned long long tot[2] = {0, 0};
+    CK(cudaMemcpyAsync(tot, h->trav_tot.p, 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    TRY(h->trav_bases.fit(tot[0] + 16));
+    TRY(h->trav_off.fit((tot[1] + 1) * 8));
+    CK(launch_traverse_write(W, h->res_keys, h->res_cls, n, h->p.k, h->trav_scratch.p, h->trav_bases.as<char>(),
+                             h->trav_off.as<unsigned long long>(), h->num_sms, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->st.launches += 8;
+    h->contig_bases = tot[0];
+    h->n_contigs = tot[1];
+    h->have_contigs = true;
+    out->n_contigs = tot[1];
+    out->bases = tot[0];
+    out->seq = h->trav_bases.as<char>();
+    out->offsets = reinterpret_cast<const uint64_t*>(h->trav_off.as<unsigned long long>());
+    return KMER_OK;
+}
+
+int kmer_analysis_copy_contigs(kmer_analysis_t* h, char* seq, uint64_t* offsets, uint64_t seq_capacity,
+                               uint64_t contig_capacity) {
+    if (!h) return fail(KMER_ERR_INVALID_ARG, "NULL handle");
+    if (!h->have_contigs) return fail(KMER_ERR_BAD_STATE, "no traversal since the last query");
+    if (seq_capacity < h->contig_bases || contig_capacity < h->n_contigs)
+        return fail(KMER_ERR_INVALID_ARG, "buffers hold %llu bases / %llu contigs, %llu / %llu needed",
+                    (unsigned long long)seq_capacity, (unsigned long long)contig_capacity, h->contig_bases,
+                    h->n_contigs);
+    DeviceGuard dg(h->device);
+    StreamScope scope(h->stream);
+    if (seq && h->contig_bases) CK(paced_copy(seq, h->trav_bases.p, h->contig_bases, h->stream));
+    if (offsets) CK(cudaMemcpyAsync(offsets, h->trav_off.p, (h->n_contigs + 1) * 8, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return KMER_OK;
+}
+
 int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const uint64_t* offsets,
                                 uint64_t n_contigs, int where, uint64_t* added, kmer_result_view* out) {
     if (!h || !out) return fail(KMER_ERR_INVALID_ARG, "NULL handle or output");
@@ -1388,6 +1453,7 @@ int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const u
         if (rc == KMER_OK) {
             h->n_out = h->host_misc->out_n;
             h->lk_cap = 0;  // the index does not cover the added k-mers
+            h->have_contigs = false;
             if (added) *added = h->n_out - n0;
         }
         if (b) kmer_analysis_destroy(b);
@@ -1424,6 +1490,7 @@ int kmer_analysis_reset(kmer_analysis_t* h) {
     for (kmer_readset* rs : h->owned) destroy_readset(rs);
     h->owned.clear();
     h->have_result = false;
+    h->have_contigs = false;
     h->n_out = 0;
     h->lk_cap = 0;
     return KMER_OK;

@@ -53,6 +53,19 @@ cudaError_t launch_merge_append(unsigned W, const unsigned long long* bkeys, con
                                 unsigned long long out_cap, unsigned long long* n_out, unsigned* status, int num_sms,
                                 cudaStream_t s);
 
+// De Bruijn graph traversal (traverse.cu) over n survivors (keys, classes)
+// with their index: plan (links, list ranking, rings, lengths; totals[0] =
+// contig bases, totals[1] = contigs, device), then write (contig bases into
+// out, contig_off = n_contigs + 1 offsets).  scratch: traverse_scratch_bytes,
+// kept between the two calls.
+size_t traverse_scratch_bytes(unsigned long long n);
+cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, const unsigned char* cls,
+                                 unsigned long long n, unsigned k, const unsigned* idx, unsigned long long cap,
+                                 void* scratch, unsigned long long* totals, int num_sms, cudaStream_t s);
+cudaError_t launch_traverse_write(unsigned W, const unsigned long long* keys, const unsigned char* cls,
+                                  unsigned long long n, unsigned k, void* scratch, char* out,
+                                  unsigned long long* contig_off, int num_sms, cudaStream_t s);
+
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
 // tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles; min_k =
 // the smallest k of the jobs (one-word keys with k >= 17 roll on their high

@@ -6,37 +6,10 @@
 // canonicalises the given k-mer (Sec. II-B: a k-mer and its reverse
 // complement are one vertex) and probes the index.
 #include "kernels.h"
+#include "keyops.cuh"
 #include "kmer_analysis.h"
 
 namespace kmer {
-
-constexpr unsigned kIdxEmpty = 0xFFFFFFFFu;
-
-template <int W>
-__device__ __forceinline__ unsigned long long key_hash(const unsigned long long (&key)[W]) {
-    unsigned long long x = 0x9E3779B97F4A7C15ull;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        x ^= key[w];
-        x *= 0xFF51AFD7ED558CCDull;
-        x ^= x >> 33;
-    }
-    return x;
-}
-
-// Base i (0 = first, most significant) of a k-mer held as W words, word 0
-// most significant.
-template <int W>
-__device__ __forceinline__ unsigned get_base(const unsigned long long (&key)[W], unsigned k, unsigned i) {
-    const unsigned pos = 2 * (k - 1 - i);  // bit position from the least significant end
-    return (unsigned)(key[W - 1 - pos / 64] >> (pos % 64)) & 3u;
-}
-
-template <int W>
-__device__ __forceinline__ void set_base(unsigned long long (&key)[W], unsigned k, unsigned i, unsigned b) {
-    const unsigned pos = 2 * (k - 1 - i);
-    key[W - 1 - pos / 64] |= (unsigned long long)b << (pos % 64);
-}
 
 template <int W>
 __global__ void __launch_bounds__(256) index_build_kernel(const unsigned long long* __restrict__ keys,
