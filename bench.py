@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--reads", type=int, default=0, help="override the number of reads (development only)")
     ap.add_argument("--variant", choices=["partitioned", "hbm_table"], default="partitioned")
     ap.add_argument("--leaf-bits", type=int, default=0)
+    ap.add_argument("--gate", action="store_true", help="single: Bloom gate (k-mers seen once kept out of counting)")
     ap.add_argument("--mode", choices=["single", "batched", "serve", "multik", "large"], default="single",
                     help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
                          "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
@@ -91,6 +92,7 @@ KERNEL_SOURCES = {
     "repart_kernel": ["repart.cu", "stage.cuh", "common.cuh", "kernels.h"],
     "leaf_kernel": ["leaf.cu", "roll.cuh", "common.cuh", "kernels.h"],
     "direct_insert_kernel": ["hbm.cu", "roll.cuh", "common.cuh", "kernels.h"],
+    "gate_kernel": ["gate.cu", "roll.cuh", "common.cuh", "kernels.h"],
 }
 
 
@@ -233,7 +235,7 @@ def config_of(args, recipe, n_bases):
     return {"workload": f"synthetic metagenome, {recipe.n_genomes} genomes, {n_bases / 1e9:.2f} Gbases, "
                         f"150 bp reads, k={args.k}",
             "reads": recipe.n_reads, "bases": n_bases, "read_len": 150, "k": args.k, "min_count": 2,
-            "qual_threshold": 20, "variant": args.variant,
+            "qual_threshold": 20, "variant": args.variant, "bloom_gate": bool(args.gate),
             "l2": "inputs (reads 4 GB, records >12 GB) larger than the 129 MB L2; no flush"}
 
 
@@ -289,7 +291,8 @@ def run_ours(args):
     variant = pkg.KMER_VARIANT_HBM_TABLE if args.variant == "hbm_table" else pkg.KMER_VARIANT_PARTITIONED
 
     rset = pkg.ReadSet(bases_d, quals_d, offs_d, stream=stream)
-    ka = pkg.KmerAnalysis(args.k, stream=stream, flags=pkg.KMER_FLAG_PROFILE, variant=variant,
+    gate_flag = pkg.KMER_FLAG_BLOOM_GATE if args.gate else 0
+    ka = pkg.KmerAnalysis(args.k, stream=stream, flags=pkg.KMER_FLAG_PROFILE | gate_flag, variant=variant,
                           leaf_bits=args.leaf_bits)
 
     def step():
