@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--variant", choices=["partitioned", "hbm_table"], default="partitioned")
     ap.add_argument("--leaf-bits", type=int, default=0)
     ap.add_argument("--gate", action="store_true", help="single: Bloom gate (k-mers seen once kept out of counting)")
+    ap.add_argument("--sorted", action="store_true", help="single: survivors in ascending key order")
     ap.add_argument("--mode", choices=["single", "batched", "serve", "multik", "large"], default="single",
                     help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
                          "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
@@ -236,6 +237,7 @@ def config_of(args, recipe, n_bases):
                         f"150 bp reads, k={args.k}",
             "reads": recipe.n_reads, "bases": n_bases, "read_len": 150, "k": args.k, "min_count": 2,
             "qual_threshold": 20, "variant": args.variant, "bloom_gate": bool(args.gate),
+            "sorted_output": bool(args.sorted),
             "l2": "inputs (reads 4 GB, records >12 GB) larger than the 129 MB L2; no flush"}
 
 
@@ -292,6 +294,8 @@ def run_ours(args):
 
     rset = pkg.ReadSet(bases_d, quals_d, offs_d, stream=stream)
     gate_flag = pkg.KMER_FLAG_BLOOM_GATE if args.gate else 0
+    if args.sorted:
+        gate_flag |= pkg.KMER_FLAG_SORTED_OUTPUT
     ka = pkg.KmerAnalysis(args.k, stream=stream, flags=pkg.KMER_FLAG_PROFILE | gate_flag, variant=variant,
                           leaf_bits=args.leaf_bits)
 
@@ -310,8 +314,8 @@ def run_ours(args):
         v = step()
         torch.cuda.synchronize()
         first_ms.append(1e3 * (time.perf_counter() - tw))
-    stage_keys = ("ms_scatter", "ms_repart", "ms_leaf", "ms_fallback", "n_scatter", "n_repart", "n_leaf",
-                  "n_fallback")
+    stage_keys = ("ms_gate", "ms_scatter", "ms_repart", "ms_leaf", "ms_fallback", "ms_sort", "n_gate", "n_scatter",
+                  "n_repart", "n_leaf", "n_fallback", "n_sort")
     acc = {k: 0.0 for k in stage_keys}
     launches = 0
     clocks = Clocks(local)

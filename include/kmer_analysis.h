@@ -131,6 +131,18 @@ typedef struct {
  * share of the windows and memory is tight.  Requires min_count >= 2 and the
  * partitioned variant (INVALID_ARG otherwise); ignored by batches. */
 #define KMER_FLAG_BLOOM_GATE 2u
+/* flags: results in ascending key order.  The k-mer set has no order of its
+ * own (Sec. II-A, use case 1: inserts commute); without this flag the
+ * survivors come out grouped by partition.  With it, query, query_into and
+ * merge_contigs leave them sorted by key (word 0 first, numerically; the
+ * same as the lexicographic order of the k-mers) with count, ext and cls
+ * moved along: a least-significant-digit radix sort on the device, 2k/8
+ * passes over the keys, in place in the result arrays.  Its scratch (about
+ * 8W + 52 bytes per survivor) reuses the query's record buffers when they are
+ * large enough.  query_into with page-locked host arrays (KMER_HOST) then
+ * stages through the analysis's device buffers as with KMER_HOST_STAGED.
+ * At most 2^32 - 2 survivors (INVALID_ARG beyond).  Ignored by batches. */
+#define KMER_FLAG_SORTED_OUTPUT 4u
 
 /* Results of the last query.  Device pointers owned by the analysis; valid
  * until the next submit, query, reset or destroy of the same handle. */
@@ -174,6 +186,8 @@ typedef struct {
                                    the counting pass kept) */
     float ms_gate;              /* with KMER_FLAG_PROFILE: device time of the gate's pass */
     uint32_t n_gate;
+    float ms_sort;              /* with KMER_FLAG_PROFILE and KMER_FLAG_SORTED_OUTPUT: device time of the sort */
+    uint32_t n_sort;
 } kmer_analysis_stats;
 
 /* Fills *p with defaults: min_count 2, qual_offset 33, qual_threshold 20,
@@ -230,8 +244,9 @@ int kmer_analysis_submit_raw(kmer_analysis_t *h, const char *bases, const uint8_
 
 /* Counts, filters and classifies everything submitted since the last reset
  * (steps a2-a7) and fills *out with device pointers to the survivors, in no
- * particular order.  Synchronises the stream.  Buffers grow as needed and
- * are kept for the next query.  Errors: OOM, TABLE_FULL, COUNTER_OVERFLOW,
+ * particular order (ascending key order with KMER_FLAG_SORTED_OUTPUT).
+ * Synchronises the stream.  Buffers grow as needed and are kept for the next
+ * query.  Errors: OOM, TABLE_FULL, COUNTER_OVERFLOW,
  * TIMEOUT, CUDA; the previous results are invalid after an error. */
 int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
 
@@ -241,12 +256,14 @@ int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
  * (where = KMER_HOST) the transfer to the host overlaps the counting.  With
  * where = KMER_HOST_STAGED (any host arrays) the survivors go to the
  * analysis's own device buffers first and are then copied to the arrays by
- * the copy engines.  The
- * arrays hold `capacity` k-mers and must not overlap; *out points at them.
- * The results stay valid (for views, copies and lookups) until the next
- * query, reset or destroy.  Errors: as kmer_analysis_query, plus
- * INVALID_ARG for NULL arrays, host arrays that are not page-locked, or more
- * survivors than `capacity` (kmer_last_error_message gives the count). */
+ * the copy engines.  The arrays hold `capacity` k-mers and must not
+ * overlap; with KMER_DEVICE and KMER_HOST the kernels write them directly,
+ * so keys must be 8-byte, count 4-byte, ext 16-byte and cls 2-byte aligned
+ * (as any allocation is).  *out points at them.  The results stay valid (for
+ * views, copies and lookups) until the next query, reset or destroy.
+ * Errors: as kmer_analysis_query, plus INVALID_ARG for NULL or misaligned
+ * arrays, host arrays that are not page-locked, or more survivors than
+ * `capacity` (kmer_last_error_message gives the count). */
 int kmer_analysis_query_into(kmer_analysis_t *h, uint64_t *keys, uint32_t *count, uint32_t *ext, uint8_t *cls,
                              uint64_t capacity, int where, kmer_result_view *out);
 

@@ -37,6 +37,7 @@ KMER_VARIANT_PARTITIONED, KMER_VARIANT_HBM_TABLE = 0, 1
 KMER_CLS_FORK, KMER_CLS_DEAD_END = 4, 5
 KMER_FLAG_PROFILE = 1
 KMER_FLAG_BLOOM_GATE = 2
+KMER_FLAG_SORTED_OUTPUT = 4
 KMER_MAX_K = 127
 
 
@@ -72,7 +73,8 @@ class kmer_analysis_stats(ctypes.Structure):
                 ("n_repart", ctypes.c_uint32), ("n_leaf", ctypes.c_uint32), ("n_fallback", ctypes.c_uint32),
                 ("records_l2", ctypes.c_uint64), ("leaf_splits", ctypes.c_uint64),
                 ("l2_waves", ctypes.c_uint64), ("gate_first", ctypes.c_uint64), ("gate_twice", ctypes.c_uint64),
-                ("ms_gate", ctypes.c_float), ("n_gate", ctypes.c_uint32)]
+                ("ms_gate", ctypes.c_float), ("n_gate", ctypes.c_uint32),
+                ("ms_sort", ctypes.c_float), ("n_sort", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -172,6 +172,7 @@ struct kmer_analysis {
     DevBuf fb_list, split_list, hbm, misc;
     DevBuf gate1, gate2, gate_cnt;  // Bloom gate: filters F1, F2 and the gate pass's counters
     DevBuf trav_scratch, trav_bases, trav_off, trav_tot;  // graph traversal: scratch and contigs
+    DevBuf sort_buf;  // sorted output: scratch when no records buffer is large enough
     unsigned long long n_contigs = 0, contig_bases = 0;
     bool have_contigs = false;
     DevBuf lk_index, lk_keys, lk_out;  // survivors' index for lookups, staging of host lookups
@@ -187,7 +188,7 @@ struct kmer_analysis {
     unsigned long long out_cap = 0, fb_cap = 0;
     Misc* host_misc = nullptr;  // pinned
     // profiling (KMER_FLAG_PROFILE): one begin/end event pair per stage
-    enum { STG_SCATTER, STG_REPART, STG_LEAF, STG_FALLBACK, STG_GATE, STG_N };
+    enum { STG_SCATTER, STG_REPART, STG_LEAF, STG_FALLBACK, STG_GATE, STG_SORT, STG_N };
     cudaEvent_t ev_b[STG_N] = {}, ev_e[STG_N] = {};
     bool ev_pending[STG_N] = {};
     // results
@@ -215,7 +216,7 @@ struct kmer_analysis {
                               &fb_list, &split_list, &hbm, &misc, &lk_index, &lk_keys, &lk_out, &d_ajob,
                               &d_sjobs, &d_tile_off, &d_leaf_off,
                               &d_job_tile_off, &gate1, &gate2, &gate_cnt, &trav_scratch, &trav_bases, &trav_off,
-                              &trav_tot};
+                              &trav_tot, &sort_buf};
         size_t t = 0;
         for (auto* b : bs) t += b->bytes;
         return t;
@@ -236,7 +237,7 @@ int validate_params(const kmer_analysis_params* p) {
         return fail(KMER_ERR_INVALID_ARG, "qual_offset and qual_threshold must fit a byte");
     if (p->leaf_bits > 22) return fail(KMER_ERR_INVALID_ARG, "leaf_bits must be <= 22");
     if (p->l1_bits > 11) return fail(KMER_ERR_INVALID_ARG, "l1_bits must be <= 11");
-    if (p->flags & ~(KMER_FLAG_PROFILE | KMER_FLAG_BLOOM_GATE))
+    if (p->flags & ~(KMER_FLAG_PROFILE | KMER_FLAG_BLOOM_GATE | KMER_FLAG_SORTED_OUTPUT))
         return fail(KMER_ERR_INVALID_ARG, "unknown flags 0x%x", p->flags);
     if ((p->flags & KMER_FLAG_BLOOM_GATE) && p->min_count < 2)
         return fail(KMER_ERR_INVALID_ARG, "the Bloom gate needs min_count >= 2 (it drops k-mers seen once)");
@@ -574,8 +575,10 @@ int prof_end(kmer_analysis* h, int stg) {
 // After the stream was synchronised: add the elapsed time of finished stages.
 int prof_collect(kmer_analysis* h) {
     if (!profiling(h)) return KMER_OK;
-    float* dst[] = {&h->st.ms_scatter, &h->st.ms_repart, &h->st.ms_leaf, &h->st.ms_fallback, &h->st.ms_gate};
-    uint32_t* cnt[] = {&h->st.n_scatter, &h->st.n_repart, &h->st.n_leaf, &h->st.n_fallback, &h->st.n_gate};
+    float* dst[] = {&h->st.ms_scatter, &h->st.ms_repart, &h->st.ms_leaf, &h->st.ms_fallback, &h->st.ms_gate,
+                    &h->st.ms_sort};
+    uint32_t* cnt[] = {&h->st.n_scatter, &h->st.n_repart, &h->st.n_leaf, &h->st.n_fallback, &h->st.n_gate,
+                       &h->st.n_sort};
     for (int i = 0; i < kmer_analysis::STG_N; ++i) {
         if (!h->ev_pending[i]) continue;
         float ms = 0.f;
@@ -969,6 +972,38 @@ int run_direct(kmer_analysis* h, unsigned long long windows) {
     }
 }
 
+// Survivors in ascending key order (KMER_FLAG_SORTED_OUTPUT, sort.cu), in
+// place in the result arrays.  The scratch is a records or table buffer of the
+// query (dead once the survivors are compacted) when one is large enough,
+// else a buffer of its own.  Synchronises the stream.
+int sort_results(kmer_analysis* h) {
+    if (!(h->p.flags & KMER_FLAG_SORTED_OUTPUT) || h->n_out < 2) return KMER_OK;
+    if (h->n_out >= 0xFFFFFFFFull) return fail(KMER_ERR_INVALID_ARG, "sorted output limited to 2^32 - 2 survivors");
+    const unsigned W = h->W();
+    const size_t need = sort_scratch_bytes(W, h->n_out);
+    void* scratch = nullptr;
+    for (DevBuf* b : {&h->l2_rec, &h->l1_rec, &h->hbm})
+        if (!scratch && b->p && b->bytes >= need) scratch = b->p;
+    if (!scratch) {
+        TRY(h->sort_buf.fit(need));
+        scratch = h->sort_buf.p;
+    }
+    Misc* m = h->misc.as<Misc>();
+    CK(cudaMemsetAsync(&m->status, 0, sizeof m->status, h->stream));
+    TRY(prof_begin(h, kmer_analysis::STG_SORT));
+    unsigned launches = 0;
+    CK(launch_sort_survivors(W, h->res_keys, h->res_count, h->res_ext, h->res_cls, h->n_out, h->p.k, scratch,
+                             &m->status, h->num_sms, &launches, h->stream));
+    TRY(prof_end(h, kmer_analysis::STG_SORT));
+    h->st.launches += launches;
+    h->lk_cap = 0;  // positions changed
+    TRY(read_misc(h));
+    TRY(prof_collect(h));
+    if (h->host_misc->status & ST_TIMEOUT) return fail(KMER_ERR_TIMEOUT, "the sort's look-back gave up");
+    if (h->host_misc->status & ST_SORT_RANGE) return fail(KMER_ERR_CUDA, "internal: sort position out of range");
+    return KMER_OK;
+}
+
 int do_query(kmer_analysis* h) {
     const auto t0 = std::chrono::steady_clock::now();
     h->have_result = false;
@@ -1027,6 +1062,7 @@ int do_query(kmer_analysis* h) {
             }
         }
     }
+    TRY(sort_results(h));
     h->out_hint = h->n_out;
     if (h->res_windows) {
         h->hist_k = h->p.k;
@@ -1211,7 +1247,9 @@ int kmer_analysis_query_into(kmer_analysis_t* h, uint64_t* keys, uint32_t* count
     DeviceGuard dg(h->device);
     StreamScope scope(h->stream);
     std::memset(out, 0, sizeof *out);
-    if (where == KMER_HOST_STAGED) {  // own device buffers, then the copy engines
+    // own device buffers, then the copy engines (also for sorted output to
+    // page-locked arrays: the sort runs in device memory)
+    if (where == KMER_HOST_STAGED || (where == KMER_HOST && (h->p.flags & KMER_FLAG_SORTED_OUTPUT))) {
         const int rc = do_query(h);
         if (rc != KMER_OK) {
             h->have_result = false;
@@ -1240,6 +1278,10 @@ int kmer_analysis_query_into(kmer_analysis_t* h, uint64_t* keys, uint32_t* count
         out->distinct = h->res_distinct;
         return KMER_OK;
     }
+    // the kernels store a survivor's tallies as two 16-byte words and its classes as one 2-byte word
+    if ((reinterpret_cast<uintptr_t>(keys) & 7) || (reinterpret_cast<uintptr_t>(count) & 3) ||
+        (reinterpret_cast<uintptr_t>(ext) & 15) || (reinterpret_cast<uintptr_t>(cls) & 1))
+        return fail(KMER_ERR_INVALID_ARG, "output arrays must be aligned: keys 8, count 4, ext 16, cls 2 bytes");
     void* ptrs[4] = {keys, count, ext, cls};
     if (where == KMER_HOST)
         for (auto& p : ptrs) {
@@ -1455,6 +1497,7 @@ int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const u
             h->lk_cap = 0;  // the index does not cover the added k-mers
             h->have_contigs = false;
             if (added) *added = h->n_out - n0;
+            if (h->n_out > n0) rc = sort_results(h);
         }
         if (b) kmer_analysis_destroy(b);
         kmer_readset_destroy(crs);

@@ -44,6 +44,7 @@ enum StatusBits : unsigned int {
     ST_TIMEOUT = 1u << 5,        // a bounded spin gave up
     ST_COUNTER_OVERFLOW = 1u << 6,
     ST_L2_PLAN = 1u << 7,        // the level-2 planner found the leaf layout larger than the buffer
+    ST_SORT_RANGE = 1u << 8,     // a radix-sort position fell outside the survivors (write skipped)
 };
 
 // Extension code of one window: left and right in {0 = none, 1..4 = A,C,G,T + 1},

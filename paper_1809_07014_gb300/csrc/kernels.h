@@ -66,6 +66,18 @@ cudaError_t launch_traverse_write(unsigned W, const unsigned long long* keys, co
                                   unsigned long long n, unsigned k, void* scratch, char* out,
                                   unsigned long long* contig_off, int num_sms, cudaStream_t s);
 
+// Survivors in ascending key order: LSD radix sort of the n keys (8-bit
+// digits over the 2k key bits, one-sweep passes, n < 2^32), then count / ext /
+// cls gathered through the permutation; all four arrays are rewritten in
+// place.  scratch: sort_scratch_bytes; *launches counts the kernels; status
+// gets ST_TIMEOUT if a look-back gave up and ST_SORT_RANGE if a position fell
+// outside [0, n) (its write skipped).  Synchronises the stream once (to skip
+// passes whose digit is constant).
+size_t sort_scratch_bytes(unsigned W, unsigned long long n);
+cudaError_t launch_sort_survivors(unsigned W, unsigned long long* keys, unsigned* count, unsigned* ext,
+                                  unsigned char* cls, unsigned long long n, unsigned k, void* scratch,
+                                  unsigned* status, int num_sms, unsigned* launches, cudaStream_t s);
+
 // Level-1 scatter (a2-a3 + partition): one CTA per read tile of 256 reads;
 // tile_off = exclusive prefix (n_jobs + 1) of the jobs' read tiles; min_k =
 // the smallest k of the jobs (one-word keys with k >= 17 roll on their high

@@ -52,7 +52,7 @@ def test_default_params(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("k", 0), ("k", 2), ("k", 128), ("k", 129), ("min_count", 0), ("err_den", 0), ("ext_mode", 2),
-    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 4), ("l1_bits", 12),
+    ("variant", 7), ("leaf_bits", 23), ("qual_threshold", 256), ("flags", 8), ("l1_bits", 12),
 ])
 def test_invalid_params_rejected_before_device(lib, field, value):
     p = pkg.make_params(31)

@@ -107,14 +107,20 @@ def fullsize():
     res = ka.results()
     st = ka.stats()
     ka.close()
+    # the same analysis with sorted output
+    ka = pkg.KmerAnalysis(K, stream=stream, flags=pkg.KMER_FLAG_SORTED_OUTPUT | pkg.KMER_FLAG_PROFILE)
+    ka.submit(r)
+    res_sorted = ka.results()
+    st_sorted = ka.stats()
+    ka.close()
     r.close()
     del dev
     torch.cuda.empty_cache()
-    return rs, res, st
+    return rs, res, st, res_sorted, st_sorted
 
 
 def test_metagenome_2gbases_k31_complete_on_hash_shards(fullsize):
-    rs, res, _ = fullsize
+    rs, res = fullsize[:2]
     p = oracle.Params(k=K)
     h = fnv1a_shard_packed(res.keys[:, 0], K)
     # the torch hash agrees with the plain vectorised FNV-1a of the decoded strings
@@ -131,7 +137,7 @@ def test_metagenome_2gbases_k31_complete_on_hash_shards(fullsize):
 
 
 def test_metagenome_2gbases_k31(fullsize):
-    rs, res, st = fullsize
+    rs, res, st = fullsize[:3]
     threads = oracle.host_threads()
     p = oracle.Params(k=K)
     n = len(res)
@@ -183,3 +189,19 @@ def test_metagenome_2gbases_k31(fullsize):
     assert (cnt[idx] == c[3000:][found]).all()
     assert (ext[idx] == e[3000:][found]).all()
     assert (res.cls[idx] == cl[3000:][found]).all()
+
+
+def test_metagenome_2gbases_k31_sorted_output(fullsize):
+    """KMER_FLAG_SORTED_OUTPUT at full size (about 10^8 survivors, 8 radix
+    passes): strictly ascending keys, and row for row the unsorted output
+    sorted on the host."""
+    _, res, _, srt, st = fullsize
+    assert len(srt) == len(res) and srt.windows == res.windows and srt.distinct == res.distinct
+    sk = srt.keys[:, 0]
+    assert (sk[1:] > sk[:-1]).all(), "sorted output not strictly ascending"
+    order = np.argsort(res.keys[:, 0])
+    assert (res.keys[order, 0] == sk).all()
+    assert (res.count[order] == srt.count).all()
+    assert (res.ext[order] == srt.ext).all()
+    assert (res.cls[order] == srt.cls).all()
+    assert st["n_sort"] == 1, st
