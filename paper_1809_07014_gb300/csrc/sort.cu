@@ -2,8 +2,11 @@
 // is a set (Sec. II-A use case 1: inserts commute), so its order is free; the
 // partitions leave it grouped by the mixed key.  A least-significant-digit
 // radix sort of the keys (8-bit digits over the 2k key bits) carries each
-// survivor's position along; the counts, tallies and classes are then
-// gathered through that permutation.
+// survivor's position along; the counts, tallies and classes travel as one
+// 64-byte record per survivor (written while the digits are counted) and are
+// gathered through that permutation straight into the result arrays, one
+// random record read per survivor (three random reads of the separate arrays
+// and a copy back took about 30 % longer on 114 M survivors).
 //
 // One kernel per digit (a one-sweep pass): each CTA takes the next tile of
 // keys, ranks them by digit within the tile (stable: warps own consecutive
@@ -24,10 +27,16 @@ namespace kmer {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr unsigned kSortSpinBudget = 1u << 22;  // look-back polls per thread before giving up
+constexpr int kLookBack = 8;                     // predecessors read per look-back step
 
 template <int W>
 struct SortShape {
-    static constexpr int ITEMS = W == 1 ? 16 : 8;  // keys per thread
+    // keys per thread and CTAs per SM (the registers are bounded for it): a
+    // pass holds only one word per key in registers, so occupancy is set by
+    // the shared-memory tile; measured on 114 M one-word keys, 8 keys at six
+    // CTAs per SM ran a pass in 0.86 ms against 1.16 ms for 12 keys at three
+    static constexpr int ITEMS = W <= 2 ? 8 : 4;
+    static constexpr int MINB = W == 1 ? 6 : 4;
     static constexpr int TILE = kSortThreads * ITEMS;
     static constexpr size_t SMEM = (size_t)TILE * W * 8 + (size_t)TILE * 4;  // reordered keys + positions
 };
@@ -44,11 +53,21 @@ __device__ __forceinline__ unsigned digit_of(const unsigned long long (&key)[W],
     return (unsigned)(v >> sh) & 0xFFu;
 }
 
-// hist[p * 256 + d] = keys whose digit p is d, for p < passes.
+// A survivor's payload while the keys are sorted, 64 bytes (written whole,
+// so no sector is partly written): (count, classes left | right << 8, 0, 0),
+// ext[0..3], ext[4..7], zeros.
+constexpr int kRecU4 = 4;
+
+// hist[p * 256 + d] = keys whose digit p is d, for p < passes; rec[i] = the
+// payload record of survivor i.
 template <int W>
 __global__ void __launch_bounds__(kSortThreads) sort_digits_kernel(const unsigned long long* __restrict__ keys,
+                                                                   const unsigned* __restrict__ count,
+                                                                   const unsigned* __restrict__ ext,
+                                                                   const unsigned char* __restrict__ cls,
                                                                    unsigned long long n, unsigned passes,
-                                                                   unsigned* __restrict__ hist) {
+                                                                   unsigned* __restrict__ hist,
+                                                                   uint4* __restrict__ rec) {
     extern __shared__ unsigned h[];  // passes * 256
     for (unsigned i = threadIdx.x; i < passes * 256; i += kSortThreads) h[i] = 0;
     __syncthreads();
@@ -57,6 +76,13 @@ __global__ void __launch_bounds__(kSortThreads) sort_digits_kernel(const unsigne
         unsigned long long key[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) key[w] = keys[i * W + w];
+        const uchar2 c2 = reinterpret_cast<const uchar2*>(cls)[i];
+        const uint4* e = reinterpret_cast<const uint4*>(ext + i * 8);
+        uint4* r = rec + i * kRecU4;
+        r[0] = make_uint4(count[i], (unsigned)c2.x | (unsigned)c2.y << 8, 0u, 0u);
+        r[1] = e[0];
+        r[2] = e[1];
+        r[3] = make_uint4(0u, 0u, 0u, 0u);
         for (unsigned p = 0; p < passes; ++p) atomicAdd(&h[p * 256 + digit_of<W>(key, p)], 1u);
     }
     __syncthreads();
@@ -97,8 +123,11 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
 // ordered by digit `pass`.  status: tiles * 256 words (stamp << 32 | count),
 // stamps 2 s + 1 (the tile's own count) and 2 s + 2 (its inclusive prefix)
 // for the s-th pass of this sort; tile_counter: zero before the pass.
+// Only the key word that holds the digit is kept in registers while ranking;
+// the keys and positions are read again (from L2) when the tile is reordered,
+// and the look-back runs after the reorder so its wait overlaps that work.
 template <int W>
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
+__global__ void __launch_bounds__(kSortThreads, SortShape<W>::MINB) sort_pass_kernel(
     const unsigned long long* __restrict__ src, const unsigned* __restrict__ isrc, unsigned long long n,
     unsigned pass, unsigned stamp_s, const unsigned* __restrict__ hist, unsigned long long* status,
     unsigned* tile_counter, unsigned long long* __restrict__ dst, unsigned* __restrict__ idst, unsigned* err) {
@@ -113,6 +142,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
     __shared__ unsigned s_tile;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned d_me = threadIdx.x;  // the digit this thread looks after in the scans
+    const unsigned wi = W - 1 - (8 * pass) / 64, sh = (8 * pass) % 64;  // the digit's word and shift
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);  // tiles in start order: predecessors run
     for (int i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -120,19 +150,13 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
     const unsigned long long t0 = t * TILE;
     const unsigned tile_n = (unsigned)(n - t0 < (unsigned long long)TILE ? n - t0 : TILE);
 
-    // ---- load and rank: warp w owns keys [w * 32 * ITEMS, (w + 1) * 32 * ITEMS) of the tile
-    unsigned long long key[ITEMS][W];
-    unsigned pos[ITEMS];  // position in the input
-    unsigned dr[ITEMS];   // digit (9 bits: 256 + lane past the end), then rank << 9 | digit
+    // ---- digits and ranks: warp w owns keys [w * 32 * ITEMS, (w + 1) * 32 * ITEMS) of the tile
+    unsigned dr[ITEMS];  // digit (9 bits: 256 + lane past the end), then rank << 9 | digit
     const unsigned long long wbase = t0 + (unsigned long long)wid * 32 * ITEMS;
 #pragma unroll
     for (int u = 0; u < ITEMS; ++u) {
         const unsigned long long i = wbase + (unsigned long long)u * 32 + lane;
-        const bool in = i < n;
-#pragma unroll
-        for (int w = 0; w < W; ++w) key[u][w] = in ? src[i * W + w] : 0ull;
-        pos[u] = in ? (isrc ? isrc[i] : (unsigned)i) : 0u;
-        dr[u] = in ? digit_of<W>(key[u], pass) : 256u + lane;  // past the end: a digit of its own
+        dr[u] = i < n ? (unsigned)(src[i * W + wi] >> sh) & 0xFFu : 256u + lane;  // past the end: a digit of its own
     }
 #pragma unroll
     for (int u = 0; u < ITEMS; ++u) {
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
     }
     __syncthreads();
 
-    // ---- tile counts per digit; publish them, then the inclusive prefix after the look-back
+    // ---- tile counts per digit: publish them; tile-local starts
     unsigned cnt = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
@@ -159,75 +183,94 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(
     const unsigned agg = 2 * stamp_s + 1, inc = 2 * stamp_s + 2;
     unsigned long long* my = status + t * 256 + d_me;
     publish(my, (unsigned long long)(t == 0 ? inc : agg) << 32 | cnt);
+    // start of the digit's run among all keys: earlier digits of this pass
+    const unsigned dstart = block_excl_scan(__ldg(hist + pass * 256 + d_me), warp_tot);
+    tstart[d_me] = block_excl_scan(cnt, warp_tot);
+    __syncthreads();
+
+    // ---- reorder the tile by digit in shared memory (keys and positions read again)
+#pragma unroll
+    for (int u = 0; u < ITEMS; ++u) {
+        const unsigned d = dr[u] & 0x1FFu;
+        if (d >= 256) continue;
+        const unsigned long long i = wbase + (unsigned long long)u * 32 + lane;
+        const unsigned lp = tstart[d] + wcnt[wid][d] + (dr[u] >> 9);
+#pragma unroll
+        for (int w = 0; w < W; ++w) skeys[(size_t)lp * W + w] = src[i * W + w];
+        sidx[lp] = isrc ? isrc[i] : (unsigned)i;
+    }
+
+    // ---- look-back: keys of this digit in earlier tiles
     unsigned long long prefix = 0;
     if (t > 0) {
+        // a window of kLookBack predecessors per step: their words are read
+        // together and summed nearest first up to the first inclusive prefix;
+        // a predecessor that has not yet published is polled again
         unsigned spins = 0;
         bool gave_up = false;
-        for (long long j = (long long)t - 1; j >= 0 && !gave_up;) {
-            const unsigned long long v = poll(status + (unsigned long long)j * 256 + d_me);
-            const unsigned s = (unsigned)(v >> 32);
-            if (s == agg || s == inc) {
-                prefix += v & 0xFFFFFFFFull;
-                if (s == inc) break;
-                --j;
-            } else if (++spins > kSortSpinBudget) {
-                gave_up = true;
-            } else {
+        long long j = (long long)t - 1;
+        for (;;) {
+            unsigned long long v[kLookBack];
+#pragma unroll
+            for (int q = 0; q < kLookBack; ++q)
+                v[q] = j - q >= 0 ? poll(status + (unsigned long long)(j - q) * 256 + d_me)
+                                  : (unsigned long long)inc << 32;  // before tile 0: an empty prefix
+            int q = 0;
+            bool done = false;
+            for (; q < kLookBack; ++q) {
+                const unsigned st = (unsigned)(v[q] >> 32);
+                if (st != agg && st != inc) break;
+                prefix += v[q] & 0xFFFFFFFFull;
+                if (st == inc) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            j -= q;
+            if (q < kLookBack) {
+                if (++spins > kSortSpinBudget) {
+                    gave_up = true;
+                    break;
+                }
                 __nanosleep(32);
             }
         }
         if (gave_up) atomicOr(err, ST_TIMEOUT);
         publish(my, (unsigned long long)inc << 32 | ((prefix + cnt) & 0xFFFFFFFFull));
     }
-    // global start of the digit's run: earlier digits of this pass, then earlier tiles
-    const unsigned dstart = block_excl_scan(__ldg(hist + pass * 256 + d_me), warp_tot);
     gbase[d_me] = (unsigned long long)dstart + prefix;
-    tstart[d_me] = block_excl_scan(cnt, warp_tot);
     __syncthreads();
 
-    // ---- reorder the tile by digit in shared memory, then write each digit's run
-#pragma unroll
-    for (int u = 0; u < ITEMS; ++u) {
-        const unsigned d = dr[u] & 0x1FFu;
-        if (d >= 256) continue;
-        const unsigned lp = tstart[d] + wcnt[wid][d] + (dr[u] >> 9);
-#pragma unroll
-        for (int w = 0; w < W; ++w) skeys[(size_t)lp * W + w] = key[u][w];
-        sidx[lp] = pos[u];
-    }
-    __syncthreads();
+    // ---- write each digit's run
     for (unsigned j = threadIdx.x; j < tile_n; j += kSortThreads) {
-        unsigned long long kk[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) kk[w] = skeys[(size_t)j * W + w];
-        const unsigned d = digit_of<W>(kk, pass);
+        const unsigned d = (unsigned)(skeys[(size_t)j * W + wi] >> sh) & 0xFFu;
         const unsigned long long g = gbase[d] + (j - tstart[d]);
         if (g >= n) {  // only after a look-back gave up: record it and skip the write
             atomicOr(err, ST_SORT_RANGE);
             continue;
         }
 #pragma unroll
-        for (int w = 0; w < W; ++w) dst[g * W + w] = kk[w];
+        for (int w = 0; w < W; ++w) dst[g * W + w] = skeys[(size_t)j * W + w];
         idst[g] = sidx[j];
     }
 }
 
-// The survivors' counts, tallies and classes in the order of `perm` (`ext`
-// 16-byte and `cls` 2-byte aligned, as the result arrays always are).
+// The survivors' counts, tallies and classes in the order of `perm`, from
+// their payload records (`ext` 16-byte and `cls` 2-byte aligned, as the
+// result arrays always are).
 __global__ void __launch_bounds__(256) sort_gather_kernel(const unsigned* __restrict__ perm, unsigned long long n,
-                                                          const unsigned* __restrict__ count,
-                                                          const unsigned* __restrict__ ext,
-                                                          const unsigned char* __restrict__ cls,
-                                                          unsigned* __restrict__ count_out, unsigned* __restrict__ ext_out,
-                                                          unsigned char* __restrict__ cls_out) {
+                                                          const uint4* __restrict__ rec,
+                                                          unsigned* __restrict__ count, unsigned* __restrict__ ext,
+                                                          unsigned char* __restrict__ cls) {
     for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
-        const unsigned long long p = perm[i];
-        count_out[i] = count[p];
-        const uint4* e = reinterpret_cast<const uint4*>(ext + p * 8);
-        uint4* eo = reinterpret_cast<uint4*>(ext_out + i * 8);
-        eo[0] = e[0];
-        eo[1] = e[1];
-        reinterpret_cast<uchar2*>(cls_out)[i] = reinterpret_cast<const uchar2*>(cls)[p];
+        const uint4* r = rec + (unsigned long long)perm[i] * kRecU4;
+        const uint4 a = r[0], e0 = r[1], e1 = r[2];
+        count[i] = a.x;
+        uint4* eo = reinterpret_cast<uint4*>(ext + i * 8);
+        eo[0] = e0;
+        eo[1] = e1;
+        reinterpret_cast<uchar2*>(cls)[i] = make_uchar2((unsigned char)(a.y & 0xFFu), (unsigned char)(a.y >> 8));
     }
 }
 
@@ -236,14 +279,17 @@ static size_t carved(size_t b) { return (b + 255) & ~size_t(255); }
 static unsigned sort_passes(unsigned k) { return (2 * k + 7) / 8; }
 
 static unsigned long long sort_tiles(unsigned W, unsigned long long n) {
-    const unsigned long long T = W == 1 ? SortShape<1>::TILE : SortShape<2>::TILE;
+    const unsigned long long T = W == 1   ? SortShape<1>::TILE
+                                 : W == 2 ? SortShape<2>::TILE
+                                 : W == 3 ? SortShape<3>::TILE
+                                          : SortShape<4>::TILE;
     return (n + T - 1) / T;
 }
 
 size_t sort_scratch_bytes(unsigned W, unsigned long long n) {
     const unsigned passes = sort_passes(32 * W);  // enough for any k of this width
     return carved(n * 8 * W) + 2 * carved(n * 4) + carved(sort_tiles(W, n) * 256 * 8) + carved(passes * 256 * 4) +
-           carved(passes * 4) + carved(n * 4) + carved(n * 32) + carved(n * 2);
+           carved(passes * 4) + carved(n * 16 * kRecU4);
 }
 
 template <int W>
@@ -265,20 +311,19 @@ static cudaError_t sort_w(unsigned long long* keys, unsigned* count, unsigned* e
     unsigned long long* st = reinterpret_cast<unsigned long long*>(carve(tiles * 256 * 8));
     unsigned* hist = reinterpret_cast<unsigned*>(carve(passes * 256 * 4));
     unsigned* counters = reinterpret_cast<unsigned*>(carve(passes * 4));
-    unsigned* cnt2 = reinterpret_cast<unsigned*>(carve(n * 4));
-    unsigned* ext2 = reinterpret_cast<unsigned*>(carve(n * 32));
-    unsigned char* cls2 = carve(n * 2);
+    uint4* rec = reinterpret_cast<uint4*>(carve(n * 16 * kRecU4));
     cudaError_t e = cudaMemsetAsync(st, 0, tiles * 256 * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, passes * 256 * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, passes * 4, s);
     if (e != cudaSuccess) return e;
-    // digit totals of every pass; passes whose digit is the same for every key move nothing
+    // digit totals of every pass (passes whose digit is the same for every key
+    // move nothing) and the payload records
     const size_t hsmem = passes * 256 * 4;
     e = cudaFuncSetAttribute(sort_digits_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     if (e != cudaSuccess) return e;
     const unsigned long long hb = (n + kSortThreads - 1) / kSortThreads;
-    const unsigned hgrid = (unsigned)(hb < (unsigned long long)num_sms * 4 ? hb : num_sms * 4);
-    sort_digits_kernel<W><<<hgrid, kSortThreads, hsmem, s>>>(keys, n, passes, hist);
+    const unsigned hgrid = (unsigned)(hb < (unsigned long long)num_sms * 16 ? hb : num_sms * 16);
+    sort_digits_kernel<W><<<hgrid, kSortThreads, hsmem, s>>>(keys, count, ext, cls, n, passes, hist, rec);
     ++*launches;
     std::vector<unsigned> h(passes * 256);
     e = cudaMemcpyAsync(h.data(), hist, h.size() * 4, cudaMemcpyDeviceToHost, s);
@@ -312,13 +357,9 @@ static cudaError_t sort_w(unsigned long long* keys, unsigned* count, unsigned* e
         if (e != cudaSuccess) return e;
     }
     const unsigned long long gb = (n + 255) / 256;
-    const unsigned g = (unsigned)(gb < (unsigned long long)num_sms * 16 ? gb : num_sms * 16);
-    sort_gather_kernel<<<g, 256, 0, s>>>(isrc, n, count, ext, cls, cnt2, ext2, cls2);
+    const unsigned g = (unsigned)(gb < (unsigned long long)num_sms * 32 ? gb : num_sms * 32);
+    sort_gather_kernel<<<g, 256, 0, s>>>(isrc, n, rec, count, ext, cls);
     ++*launches;
-    e = cudaMemcpyAsync(count, cnt2, n * 4, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ext, ext2, n * 32, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cls, cls2, n * 2, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
