@@ -506,6 +506,8 @@ def run_ours(args):
                                           f"(one FNV-1a shard per core, each walking every read), {dt:.1f} s on "
                                           f"{cores} host cores"}
     ka.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["assembly"] = assembly_record(rset, args.k, stream)
     rset.close()
     del bases_d, quals_d, offs_d
     # ---- the batched, served and multi-k forms on the same GPU (rank 0 at N = 1),
@@ -532,6 +534,61 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# -------------------------------------------------------- assembly steps
+def assembly_record(rset, k: int, stream, s_step: int = 2, reps: int = 3) -> dict:
+    """The steps of Algorithm 1 around k-mer analysis, on the survivors of the
+    bench workload (resident readset): the survivors sorted by key
+    (KMER_FLAG_SORTED_OUTPUT, device time of the sort), the de Bruijn graph
+    traversal into contigs (Sec. II-C), and the merge of those contigs'
+    (k + s)-mers into the analysis at k + s (Sec. II-G).  Host-timed
+    synchronous calls, median of `reps` after one warm-up."""
+    import torch
+
+    import paper_1809_07014_gb300 as pkg
+
+    out = {}
+    ka = pkg.KmerAnalysis(k, stream=stream, flags=pkg.KMER_FLAG_SORTED_OUTPUT | pkg.KMER_FLAG_PROFILE)
+    ms_sort = []
+    for i in range(reps + 1):
+        ka.reset(); ka.submit(rset)
+        v = ka.query()
+        if i:
+            ms_sort.append(ka.stats()["ms_sort"])
+    n = int(v.n)
+    out["sort"] = {"survivors": n, "ms": round(statistics.median(ms_sort), 3),
+                   "keys_per_s": n / (statistics.median(ms_sort) / 1e3)}
+    ms_trav = []
+    for i in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cv = pkg.kmer_analysis_traverse(ka.handle)
+        if i:
+            ms_trav.append(1e3 * (time.perf_counter() - t0))
+    out["traverse"] = {"k": k, "vertices_in": n, "contigs": int(cv.n_contigs), "contig_bases": int(cv.bases),
+                       "ms": round(statistics.median(ms_trav), 3),
+                       "k-mers_per_s": n / (statistics.median(ms_trav) / 1e3)}
+    # merge the contigs' (k + s)-mers into the analysis at k + s
+    k2 = k + s_step
+    kb = pkg.KmerAnalysis(k2, stream=stream)
+    ms_merge, added = [], 0
+    for i in range(reps + 1):
+        kb.reset(); kb.submit(rset)
+        kb.query()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        added, mv = pkg.kmer_analysis_merge_contigs(kb.handle, cv.seq, cv.offsets, int(cv.n_contigs),
+                                                   pkg.KMER_DEVICE)
+        if i:
+            ms_merge.append(1e3 * (time.perf_counter() - t0))
+    contig_kmers = max(0, int(cv.bases) - int(cv.n_contigs) * (k2 - 1))
+    out["merge"] = {"k": k2, "contigs": int(cv.n_contigs), "contig_windows_at_most": contig_kmers,
+                    "added": int(added), "merged_set": int(mv.n), "ms": round(statistics.median(ms_merge), 3)}
+    out["note"] = "host-timed synchronous calls (traverse, merge) and device time of the sort stage; median of 3"
+    kb.close()
+    ka.close()
+    return out
 
 
 # --------------------------------------------------------------- batched

@@ -1400,8 +1400,8 @@ int kmer_analysis_traverse(kmer_analysis_t* h, kmer_contigs_view* out) {
     CK(cudaStreamSynchronize(h->stream));
     TRY(h->trav_bases.fit(tot[0] + 16));
     TRY(h->trav_off.fit((tot[1] + 1) * 8));
-    CK(launch_traverse_write(W, h->res_keys, h->res_cls, n, h->p.k, h->trav_scratch.p, h->trav_bases.as<char>(),
-                             h->trav_off.as<unsigned long long>(), h->num_sms, h->stream));
+    CK(launch_traverse_write(W, h->res_keys, h->res_cls, n, h->p.k, tot[1], h->trav_scratch.p,
+                             h->trav_bases.as<char>(), h->trav_off.as<unsigned long long>(), h->num_sms, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->st.launches += 8;
     h->contig_bases = tot[0];
@@ -1450,9 +1450,65 @@ int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const u
         // bytes, offset 0, threshold 0), no count filter, and classes by the
         // static rule with t_ext = 1: a side is UNIQUE when one base follows it
         // anywhere in the contigs, DEAD_END when none, FORK when several
+        // A contig longer than kMergePiece bases is cut into pieces of that
+        // many bases overlapping by k + 1, since one thread rolls the windows of
+        // one read and contigs can be millions of bases long.  Each window and
+        // both its extension bases then lie whole in some piece; a window at a
+        // piece's edge may come twice, once without the base beyond the edge,
+        // which adds no base to its sides, and counts are not used.
+        constexpr unsigned long long kMergePiece = 4096;
+        std::vector<unsigned long long> off(n_contigs + 1);
+        if (where == KMER_DEVICE) {
+            CK(cudaMemcpyAsync(off.data(), offsets, off.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        } else {
+            std::memcpy(off.data(), offsets, off.size() * 8);
+        }
+        std::vector<unsigned long long> psrc, pdst(1, 0);
+        bool cut = false;
+        for (uint64_t c = 0; c < n_contigs; ++c) {
+            const unsigned long long a = off[c], e = off[c + 1];
+            if (e < a) return fail(KMER_ERR_INVALID_ARG, "contig offsets decrease at %llu", (unsigned long long)c);
+            cut |= e - a > kMergePiece;
+            for (unsigned long long st = a;;) {
+                const unsigned long long en = std::min(e, st + kMergePiece);
+                psrc.push_back(st);
+                pdst.push_back(pdst.back() + (en - st));
+                if (en >= e) break;
+                st = en - (h->p.k + 1);
+            }
+        }
+        DevBuf d_pieces, d_psrc, d_pdst;
+        std::vector<char> h_pieces;
+        const char* cseq = contigs;
+        const uint64_t* coff = offsets;
+        uint64_t n_seq = n_contigs;
+        int cwhere = where;
+        if (cut) {
+            const unsigned long long n_p = psrc.size(), bytes = pdst.back();
+            if (where == KMER_DEVICE) {
+                TRY(d_pieces.ensure(bytes + 16));
+                TRY(d_psrc.ensure(n_p * 8));
+                TRY(d_pdst.ensure((n_p + 1) * 8));
+                CK(cudaMemcpyAsync(d_psrc.p, psrc.data(), n_p * 8, cudaMemcpyHostToDevice, h->stream));
+                CK(cudaMemcpyAsync(d_pdst.p, pdst.data(), (n_p + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+                CK(launch_piece_copy(contigs, d_psrc.as<unsigned long long>(), d_pdst.as<unsigned long long>(), n_p,
+                                     d_pieces.as<char>(), h->num_sms, h->stream));
+                h->st.launches++;
+                cseq = d_pieces.as<char>();
+                coff = reinterpret_cast<const uint64_t*>(d_pdst.p);
+            } else {
+                h_pieces.resize(bytes);
+                for (unsigned long long i = 0; i < n_p; ++i)
+                    std::memcpy(h_pieces.data() + pdst[i], contigs + psrc[i], pdst[i + 1] - pdst[i]);
+                cseq = h_pieces.data();
+                coff = reinterpret_cast<const uint64_t*>(pdst.data());
+                cwhere = KMER_HOST_STAGED;
+            }
+            n_seq = n_p;
+        }
         kmer_readset_t* crs = nullptr;
-        TRY(make_readset(contigs, reinterpret_cast<const uint8_t*>(contigs), offsets, n_contigs, 0, 0, where,
-                         h->stream, &crs));
+        TRY(make_readset(cseq, reinterpret_cast<const uint8_t*>(cseq), coff, n_seq, 0, 0, cwhere, h->stream, &crs));
         kmer_analysis_params cp;
         kmer_analysis_default_params(&cp, h->p.k);
         cp.min_count = 1;

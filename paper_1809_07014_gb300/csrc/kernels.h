@@ -2,9 +2,31 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 
 namespace kmer {
+
+// A kernel's dynamic shared-memory limit is one attribute per function and
+// device, shared by every host thread: raise it to `bytes` when it is lower,
+// never lower it (a thread that lowered it could make another thread's launch
+// with a larger size fail).
+inline cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 constexpr int kLenExact = 128;            // read lengths below this are histogrammed exactly
 constexpr int kLenHist = kLenExact + 2;   // + count and sum of longer reads
@@ -47,6 +69,10 @@ cudaError_t launch_gate(const Job& j, unsigned long long* f1, unsigned long long
 // bcls; bn of them) absent from the indexed survivors are appended to them
 // from position *n_out on (count 0, zero tallies, their own classes); a
 // position past out_cap sets bit 0 of *status.
+// Pieces of a byte string: piece i is src[psrc[i] ..) of pdst[i + 1] - pdst[i]
+// bytes, written to dst[pdst[i] ..) (pdst: n_pieces + 1 offsets).
+cudaError_t launch_piece_copy(const char* src, const unsigned long long* psrc, const unsigned long long* pdst,
+                              unsigned long long n_pieces, char* dst, int num_sms, cudaStream_t s);
 cudaError_t launch_merge_append(unsigned W, const unsigned long long* bkeys, const unsigned char* bcls,
                                 unsigned long long bn, const unsigned* idx, unsigned long long cap,
                                 unsigned long long* keys, unsigned* count, unsigned* ext, unsigned char* cls,
@@ -63,8 +89,8 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
                                  unsigned long long n, unsigned k, const unsigned* idx, unsigned long long cap,
                                  void* scratch, unsigned long long* totals, int num_sms, cudaStream_t s);
 cudaError_t launch_traverse_write(unsigned W, const unsigned long long* keys, const unsigned char* cls,
-                                  unsigned long long n, unsigned k, void* scratch, char* out,
-                                  unsigned long long* contig_off, int num_sms, cudaStream_t s);
+                                  unsigned long long n, unsigned k, unsigned long long n_contigs, void* scratch,
+                                  char* out, unsigned long long* contig_off, int num_sms, cudaStream_t s);
 
 // Survivors in ascending key order: LSD radix sort of the n keys (8-bit
 // digits over the 2k key bits, one-sweep passes, n < 2^32), then count / ext /

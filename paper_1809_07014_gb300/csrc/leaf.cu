@@ -591,7 +591,7 @@ template <int W>
 static cudaError_t launch_leaf_w(const Job* jobs, const unsigned long long* leaf_off, unsigned n_jobs,
                                  unsigned long long leaves, unsigned cap_max, int num_sms, cudaStream_t s) {
     const size_t smem = leaf_smem_bytes(W, cap_max);
-    cudaError_t e = cudaFuncSetAttribute(leaf_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)leaf_kernel<W>, smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (unsigned long long)num_sms * 2;
     if (grid > leaves) grid = leaves;
@@ -605,7 +605,7 @@ static cudaError_t launch_leaf_split_w(const Job* jobs, unsigned n_jobs, unsigne
                                        cudaStream_t s) {
     const size_t smem = leaf_smem_bytes(W, cap_max);
     cudaError_t e =
-        cudaFuncSetAttribute(leaf_split_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void*)leaf_split_kernel<W>, smem);
     if (e != cudaSuccess) return e;
     if (n_jobs == 0) return cudaSuccess;
     leaf_split_kernel<W><<<(unsigned)num_sms * 2, kLeafThreads, smem, s>>>(jobs, n_jobs, cap_max);

@@ -166,6 +166,26 @@ cudaError_t launch_index_build(unsigned W, const unsigned long long* keys, unsig
     return cudaGetLastError();
 }
 
+// Bytes of piece i: src[psrc[i] .. psrc[i] + (pdst[i + 1] - pdst[i])) copied
+// to dst[pdst[i] ..); one CTA per piece at a time.
+__global__ void __launch_bounds__(256) piece_copy_kernel(const char* __restrict__ src,
+                                                         const unsigned long long* __restrict__ psrc,
+                                                         const unsigned long long* __restrict__ pdst,
+                                                         unsigned long long n_pieces, char* __restrict__ dst) {
+    for (unsigned long long i = blockIdx.x; i < n_pieces; i += gridDim.x) {
+        const unsigned long long a = psrc[i], b0 = pdst[i], len = pdst[i + 1] - b0;
+        for (unsigned long long j = threadIdx.x; j < len; j += 256) dst[b0 + j] = src[a + j];
+    }
+}
+
+cudaError_t launch_piece_copy(const char* src, const unsigned long long* psrc, const unsigned long long* pdst,
+                              unsigned long long n_pieces, char* dst, int num_sms, cudaStream_t s) {
+    if (n_pieces == 0) return cudaSuccess;
+    const unsigned long long g = n_pieces < (unsigned long long)num_sms * 16 ? n_pieces : (unsigned long long)num_sms * 16;
+    piece_copy_kernel<<<(unsigned)g, 256, 0, s>>>(src, psrc, pdst, n_pieces, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge_append(unsigned W, const unsigned long long* bkeys, const unsigned char* bcls,
                                 unsigned long long bn, const unsigned* idx, unsigned long long cap,
                                 unsigned long long* keys, unsigned* count, unsigned* ext, unsigned char* cls,

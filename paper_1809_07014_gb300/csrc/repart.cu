@@ -396,7 +396,7 @@ static cudaError_t launch_repart_wp(const Job* jobs, const unsigned long long* j
                                     unsigned max_p2, int num_sms, cudaStream_t s) {
     const size_t smem = repart_smem_bytes(W, max_p2);
     cudaError_t e =
-        cudaFuncSetAttribute(repart_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void*)repart_kernel<W, MAXPER>, smem);
     if (e != cudaSuccess) return e;
     repart_kernel<W, MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
     return cudaGetLastError();
@@ -407,7 +407,7 @@ static cudaError_t launch_repart_tma(const Job* jobs, const unsigned long long* 
                                      unsigned max_p2, int num_sms, cudaStream_t s) {
     const size_t smem = repart_tma_smem_bytes(W, 1u << max_p2);
     cudaError_t e =
-        cudaFuncSetAttribute(repart_tma_kernel<W, MAXPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void*)repart_tma_kernel<W, MAXPER>, smem);
     if (e != cudaSuccess) return e;
     repart_tma_kernel<W, MAXPER><<<num_sms * 2, kRepartThreads, smem, s>>>(jobs, job_tile_off, n_jobs, 1u << max_p2);
     return cudaGetLastError();

@@ -110,8 +110,7 @@ template <int W, unsigned MAXPER, bool HI, bool GATE>
 static cudaError_t launch_scatter_wpg(const Job* jobs, const unsigned long long* tile_off, unsigned n_jobs,
                                       unsigned long long tiles, unsigned max_p1, cudaStream_t s) {
     const size_t smem = scatter_smem_bytes(W, max_p1);
-    cudaError_t e = cudaFuncSetAttribute(scatter_kernel<W, MAXPER, HI, GATE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)scatter_kernel<W, MAXPER, HI, GATE>, smem);
     if (e != cudaSuccess) return e;
     if (tiles == 0) return cudaSuccess;
     if (tiles > 0x7FFFFFFFull) return cudaErrorInvalidValue;

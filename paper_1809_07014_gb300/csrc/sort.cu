@@ -319,7 +319,7 @@ static cudaError_t sort_w(unsigned long long* keys, unsigned* count, unsigned* e
     // digit totals of every pass (passes whose digit is the same for every key
     // move nothing) and the payload records
     const size_t hsmem = passes * 256 * 4;
-    e = cudaFuncSetAttribute(sort_digits_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+    e = raise_smem_limit((const void*)sort_digits_kernel<W>, hsmem);
     if (e != cudaSuccess) return e;
     const unsigned long long hb = (n + kSortThreads - 1) / kSortThreads;
     const unsigned hgrid = (unsigned)(hb < (unsigned long long)num_sms * 16 ? hb : num_sms * 16);
@@ -329,7 +329,7 @@ static cudaError_t sort_w(unsigned long long* keys, unsigned* count, unsigned* e
     e = cudaMemcpyAsync(h.data(), hist, h.size() * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sort_pass_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::SMEM);
+    e = raise_smem_limit((const void*)sort_pass_kernel<W>, Shape::SMEM);
     if (e != cudaSuccess) return e;
     // keys move from `keys` to the scratch and back, pass by pass (a final
     // copy into `keys` when the number of passes that moved is odd)

@@ -14,16 +14,22 @@
 //
 //  1. links: one kernel looks up both neighbours of every vertex in the
 //     survivors' index and keeps mutual ones (port -> partner port);
-//  2. list ranking: pointer doubling over ports gives, for every port, the end
-//     reached by walking out of it and the number of steps, in log2(n) rounds;
+//  2. list ranking: pointer jumping over ports gives, for every port, the end
+//     reached by walking out of it and the number of steps.  The walks are
+//     updated in place (a port may read a partner's walk from this round or
+//     the last: both are true statements about the path, so the result is the
+//     same and converges at least as fast), and each round visits only the
+//     ports whose walk has not reached an end: most chains are short, so the
+//     work is far below ports x log2(n);
 //  3. rings (ports whose walk never ends) are cut before their smallest
 //     canonical k-mer (found by doubling a running minimum around the ring),
-//     and the ranking is run again;
+//     and only their ports are ranked again;
 //  4. every chain is written from its end with the smaller index: the end's
 //     k-mer, then one base per later vertex at its distance from the end; the
 //     chains' lengths are scanned into offsets;
 //  5. every contig is turned into the smaller of itself and its reverse
-//     complement.
+//     complement, in chunks of 256 positions spread over the whole grid (a
+//     contig can be millions of bases long).
 #include "kernels.h"
 #include "keyops.cuh"
 
@@ -89,83 +95,130 @@ __global__ void __launch_bounds__(256) links_kernel(const unsigned long long* __
     }
 }
 
-// Walk state of a port P: after dist steps out of P the walk stands at
-// port-code `at` (a vertex and the port it would leave by next); dist 0 = P
-// has no partner (the walk ends at once).
-struct Walk {
-    unsigned at, dist;
-};
+// Walk state of a port P, one 64-bit word (dist << 32 | at), read and written
+// whole: after dist steps out of P the walk stands at port-code `at` (a vertex
+// and the port it would leave by next); dist 0 = P has no partner (the walk
+// ends at once).
+__device__ __forceinline__ unsigned long long walk_pack(unsigned at, unsigned dist) {
+    return (unsigned long long)dist << 32 | at;
+}
+__device__ __forceinline__ unsigned walk_at(unsigned long long w) { return (unsigned)w; }
+__device__ __forceinline__ unsigned walk_dist(unsigned long long w) { return (unsigned)(w >> 32); }
 
+// Appends val to list when pred holds: one atomic per warp.
+__device__ __forceinline__ void append_if(bool pred, unsigned val, unsigned* list, unsigned* count) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+// First walks: one step to the partner's other port; linked ports go to the
+// active list.
 __global__ void __launch_bounds__(256) walk_init_kernel(const unsigned* __restrict__ link, unsigned long long ports,
-                                                        Walk* __restrict__ wk) {
+                                                        unsigned long long* __restrict__ wk, unsigned* act,
+                                                        unsigned* cnt) {
     for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
         const unsigned L = link[P];
         // arriving at the partner port, the walk leaves its vertex by the other port
-        wk[P] = L == kNoPort ? Walk{(unsigned)P, 0u} : Walk{L ^ 1u, 1u};
+        wk[P] = L == kNoPort ? walk_pack((unsigned)P, 0u) : walk_pack(L ^ 1u, 1u);
+        append_if(L != kNoPort, (unsigned)P, act, cnt);
     }
 }
 
-// One round of pointer doubling: follow the walk from where it stands.
-__global__ void __launch_bounds__(256) walk_double_kernel(const Walk* __restrict__ in, unsigned long long ports,
-                                                          unsigned cap_dist, Walk* __restrict__ out) {
-    for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
-        Walk w = in[P];
-        if (w.dist) {
-            const Walk f = in[w.at];
-            if (f.dist) {
-                const unsigned long long d = (unsigned long long)w.dist + f.dist;
-                w.at = f.at;
-                w.dist = d > cap_dist ? cap_dist : (unsigned)d;
-            }
+// The same for the ports of a list (the rings, after their cut).
+__global__ void __launch_bounds__(256) walk_reinit_kernel(const unsigned* __restrict__ link,
+                                                          const unsigned* __restrict__ list,
+                                                          const unsigned* __restrict__ list_n,
+                                                          unsigned long long* __restrict__ wk, unsigned* act,
+                                                          unsigned* cnt) {
+    const unsigned n = *list_n;
+    for (unsigned i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
+        const unsigned P = list[i], L = link[P];
+        wk[P] = L == kNoPort ? walk_pack(P, 0u) : walk_pack(L ^ 1u, 1u);
+        append_if(L != kNoPort, P, act, cnt);
+    }
+}
+
+// One round of pointer jumping over the active ports, in place.  A port
+// whose walk stands at an end leaves the list; so does one whose walk reached
+// cap_dist (it goes round a ring).
+__global__ void __launch_bounds__(256) walk_jump_kernel(unsigned long long* wk, const unsigned* __restrict__ act_in,
+                                                        const unsigned* __restrict__ cnt_in, unsigned cap_dist,
+                                                        unsigned* act_out, unsigned* cnt_out) {
+    const unsigned n = *cnt_in;
+    for (unsigned i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
+        const unsigned P = act_in[i];
+        const unsigned long long w = __ldcg(wk + P);
+        const unsigned long long f = __ldcg(wk + walk_at(w));
+        bool keep = false;
+        if (walk_dist(f)) {
+            const unsigned long long d = (unsigned long long)walk_dist(w) + walk_dist(f);
+            __stcg(wk + P, walk_pack(walk_at(f), d > cap_dist ? cap_dist : (unsigned)d));
+            keep = d < cap_dist;
         }
-        out[P] = w;
+        append_if(keep, P, act_out, cnt_out);
     }
 }
 
 // Rings: per port P of a ring vertex, the smallest vertex (by key) among the
 // 2^r vertices met walking out of P, and where that walk stands; doubled like
 // the walks.  Once 2^r passes a ring's length every port of it holds the
-// ring's smallest vertex.  Ports of chain vertices keep kNoPort.
-__global__ void __launch_bounds__(256) ring_init_kernel(const Walk* __restrict__ wk, unsigned long long ports,
-                                                        unsigned cap_dist, const unsigned* __restrict__ link,
-                                                        unsigned* __restrict__ rmin, Walk* __restrict__ step) {
+// ring's smallest vertex.  The ring ports go to a list; only they are read.
+__global__ void __launch_bounds__(256) ring_init_kernel(const unsigned long long* __restrict__ wk,
+                                                        unsigned long long ports, unsigned cap_dist,
+                                                        const unsigned* __restrict__ link, unsigned* __restrict__ rmin,
+                                                        unsigned long long* __restrict__ step, unsigned* ring,
+                                                        unsigned* ring_n) {
     for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
-        const bool ring = wk[P].dist >= cap_dist;
-        rmin[P] = ring ? (unsigned)(P >> 1) : kNoPort;
-        step[P] = ring ? Walk{link[P] ^ 1u, 1u} : Walk{kNoPort, 0u};
+        const bool on_ring = walk_dist(wk[P]) >= cap_dist;
+        if (on_ring) {
+            rmin[P] = (unsigned)(P >> 1);
+            step[P] = walk_pack(link[P] ^ 1u, 1u);
+        }
+        append_if(on_ring, (unsigned)P, ring, ring_n);
     }
 }
 
 template <int W>
 __global__ void __launch_bounds__(256) ring_double_kernel(const unsigned* __restrict__ rmin_in,
-                                                          const Walk* __restrict__ step_in, unsigned long long ports,
+                                                          const unsigned long long* __restrict__ step_in,
+                                                          const unsigned* __restrict__ ring,
+                                                          const unsigned* __restrict__ ring_n,
                                                           const unsigned long long* __restrict__ keys,
-                                                          unsigned* __restrict__ rmin_out, Walk* __restrict__ step_out) {
-    for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
+                                                          unsigned* __restrict__ rmin_out,
+                                                          unsigned long long* __restrict__ step_out) {
+    const unsigned n = *ring_n;
+    for (unsigned i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
+        const unsigned P = ring[i];
         unsigned m = rmin_in[P];
-        Walk s = step_in[P];
-        if (m != kNoPort) {
-            const unsigned mv = rmin_in[s.at];  // the next 2^r vertices, from where the walk stands
-            unsigned long long a[W], b[W];
+        const unsigned at = walk_at(step_in[P]);
+        const unsigned mv = rmin_in[at];  // the next 2^r vertices, from where the walk stands
+        unsigned long long a[W], b[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                a[w] = keys[(unsigned long long)m * W + w];
-                b[w] = keys[(unsigned long long)mv * W + w];
-            }
-            if (key_less<W>(b, a)) m = mv;
-            s = Walk{step_in[s.at].at, 0u};
+        for (int w = 0; w < W; ++w) {
+            a[w] = keys[(unsigned long long)m * W + w];
+            b[w] = keys[(unsigned long long)mv * W + w];
         }
+        if (key_less<W>(b, a)) m = mv;
         rmin_out[P] = m;
-        step_out[P] = s;
+        step_out[P] = walk_pack(walk_at(step_in[at]), 0u);
     }
 }
 
-// Cut every ring before its smallest vertex: drop the link of that vertex's
-// port 0 and its partner's.
-__global__ void __launch_bounds__(256) ring_cut_kernel(const unsigned* __restrict__ rmin, unsigned long long n,
-                                                       unsigned* __restrict__ link) {
-    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
-        if (rmin[2 * i + 1] != (unsigned)i) continue;
+// Cut every ring before its smallest vertex i: drop the link of i's port 0
+// and its partner's (i's port 1 is on the list and names i as the minimum).
+__global__ void __launch_bounds__(256) ring_cut_kernel(const unsigned* __restrict__ rmin,
+                                                       const unsigned* __restrict__ ring,
+                                                       const unsigned* __restrict__ ring_n, unsigned* __restrict__ link) {
+    const unsigned n = *ring_n;
+    for (unsigned j = blockIdx.x * 256u + threadIdx.x; j < n; j += gridDim.x * 256u) {
+        const unsigned P = ring[j], i = P >> 1;
+        if (!(P & 1u) || rmin[P] != i) continue;
         const unsigned L = link[2 * i];
         if (L != kNoPort) link[L] = kNoPort;
         link[2 * i] = kNoPort;
@@ -173,26 +226,27 @@ __global__ void __launch_bounds__(256) ring_cut_kernel(const unsigned* __restric
 }
 
 // Chain of vertex i: its two ends, distances, head (the end with the smaller
-// index) and i's place.  len[i] = bases of i's contig if i is a head, else 0.
-__device__ __forceinline__ void chain_of(const Walk* wk, unsigned i, unsigned& head, unsigned& pos, bool& fwd,
-                                         unsigned& m) {
-    const Walk a = wk[2 * i], b = wk[2 * i + 1];
-    const unsigned h0 = a.dist ? a.at >> 1 : i, h1 = b.dist ? b.at >> 1 : i;
-    m = a.dist + b.dist + 1;
+// index) and i's place.
+__device__ __forceinline__ void chain_of(const unsigned long long* wk, unsigned i, unsigned& head, unsigned& pos,
+                                         bool& fwd, unsigned& m) {
+    const unsigned long long a = wk[2 * (unsigned long long)i], b = wk[2 * (unsigned long long)i + 1];
+    const unsigned h0 = walk_dist(a) ? walk_at(a) >> 1 : i, h1 = walk_dist(b) ? walk_at(b) >> 1 : i;
+    m = walk_dist(a) + walk_dist(b) + 1;
     if (h0 <= h1) {  // walking from the head reaches i through its port 0: i read as stored
         head = h0;
-        pos = a.dist;
+        pos = walk_dist(a);
         fwd = true;
     } else {
         head = h1;
-        pos = b.dist;
+        pos = walk_dist(b);
         fwd = false;
     }
 }
 
-__global__ void __launch_bounds__(256) chain_len_kernel(const Walk* __restrict__ wk, const unsigned char* __restrict__ cls,
-                                                        unsigned long long n, unsigned k,
-                                                        unsigned long long* __restrict__ len) {
+// len[i] = bases of i's contig if i is a head, else 0.
+__global__ void __launch_bounds__(256) chain_len_kernel(const unsigned long long* __restrict__ wk,
+                                                        const unsigned char* __restrict__ cls, unsigned long long n,
+                                                        unsigned k, unsigned long long* __restrict__ len) {
     for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
         unsigned long long L = 0;
         if (is_vertex(cls, i)) {
@@ -208,7 +262,7 @@ __global__ void __launch_bounds__(256) chain_len_kernel(const Walk* __restrict__
 // Bases of every contig: the head's k-mer (in the orientation that leaves
 // by its linked port), then each later vertex's last base at its distance.
 template <int W>
-__global__ void __launch_bounds__(256) chain_write_kernel(const Walk* __restrict__ wk,
+__global__ void __launch_bounds__(256) chain_write_kernel(const unsigned long long* __restrict__ wk,
                                                           const unsigned char* __restrict__ cls,
                                                           const unsigned long long* __restrict__ keys,
                                                           unsigned long long n, unsigned k,
@@ -226,7 +280,7 @@ __global__ void __launch_bounds__(256) chain_write_kernel(const Walk* __restrict
         char* c = out + off[head];
         if (head == i) {
             // the head leaves by port 1 (read as stored) unless only its port 0 is linked
-            const bool stored = m == 1 || wk[2 * i + 1].dist > 0;
+            const bool stored = m == 1 || walk_dist(wk[2 * i + 1]) > 0;
             for (unsigned b = 0; b < k; ++b)
                 c[b] = stored ? kBase[get_base<W>(x, k, b)] : kBase[3u - get_base<W>(x, k, k - 1 - b)];
         } else {
@@ -239,31 +293,86 @@ __device__ __forceinline__ char comp_base(char b) {
     return b == 'A' ? 'T' : (b == 'C' ? 'G' : (b == 'G' ? 'C' : 'A'));
 }
 
-// Each contig becomes the smaller of itself and its reverse complement.
-__global__ void __launch_bounds__(256) canon_contig_kernel(const unsigned long long* __restrict__ len,
-                                                           const unsigned long long* __restrict__ off,
-                                                           unsigned long long n, char* __restrict__ out) {
-    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
-        const unsigned long long L = len[i];
-        if (!L) continue;
-        char* c = out + off[i];
-        int cmp = 0;  // sign of rc(c) - c at the first difference
-        for (unsigned long long a = 0; a < L && !cmp; ++a) {
-            const char r = comp_base(c[L - 1 - a]);
-            if (r != c[a]) cmp = r < c[a] ? -1 : 1;
-        }
-        if (cmp >= 0) continue;
-        for (unsigned long long a = 0, b = L - 1; a <= b && b < L; ++a, --b) {
-            const char ca = c[a], cb = c[b];
-            c[a] = comp_base(cb);
-            c[b] = comp_base(ca);
-            if (b == 0) break;
+constexpr unsigned kCanonChunk = 256;  // positions of a contig's first half per work item
+
+// chunks[c] = work items of contig c: its first ceil(L / 2) positions in
+// chunks of kCanonChunk; first[c] = no difference found yet.
+__global__ void __launch_bounds__(256) canon_chunks_kernel(const unsigned long long* __restrict__ coff,
+                                                           unsigned long long nc,
+                                                           unsigned long long* __restrict__ chunks,
+                                                           unsigned long long* __restrict__ first) {
+    for (unsigned long long c = blockIdx.x * 256ull + threadIdx.x; c < nc; c += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long half = (coff[c + 1] - coff[c] + 1) / 2;
+        chunks[c] = (half + kCanonChunk - 1) / kCanonChunk;
+        first[c] = ~0ull;
+    }
+}
+
+// Work item t: its contig (the last c with cstart[c] <= t) and chunk.
+__device__ __forceinline__ unsigned long long item_contig(const unsigned long long* cstart, unsigned long long nc,
+                                                          unsigned long long t) {
+    unsigned long long lo = 0, hi = nc;  // cstart[lo] <= t < cstart[hi]
+    while (hi - lo > 1) {
+        const unsigned long long mid = (lo + hi) / 2;
+        if (cstart[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// first[c] = the first position a of contig c where c[a] differs from its
+// reverse complement's a-th base, complement(c[L - 1 - a]).
+__global__ void __launch_bounds__(256) canon_diff_kernel(const unsigned long long* __restrict__ coff,
+                                                         const unsigned long long* __restrict__ cstart,
+                                                         unsigned long long nc, unsigned long long items,
+                                                         const char* __restrict__ out,
+                                                         unsigned long long* __restrict__ first) {
+    for (unsigned long long t = blockIdx.x * 256ull + threadIdx.x; t < items; t += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long c = item_contig(cstart, nc, t);
+        const unsigned long long b0 = coff[c], L = coff[c + 1] - b0, half = (L + 1) / 2;
+        const unsigned long long a0 = (t - cstart[c]) * kCanonChunk;
+        const unsigned long long a1 = a0 + kCanonChunk < half ? a0 + kCanonChunk : half;
+        for (unsigned long long a = a0; a < a1; ++a)
+            if (comp_base(out[b0 + L - 1 - a]) != out[b0 + a]) {
+                atomicMin(first + c, a);
+                break;
+            }
+    }
+}
+
+// Whether each contig is replaced by its reverse complement: smaller at the
+// first difference (decided before any base moves).
+__global__ void __launch_bounds__(256) canon_decide_kernel(const unsigned long long* __restrict__ coff,
+                                                           unsigned long long nc, const char* __restrict__ out,
+                                                           unsigned long long* __restrict__ first) {
+    for (unsigned long long c = blockIdx.x * 256ull + threadIdx.x; c < nc; c += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long f = first[c];
+        if (f == ~0ull) continue;  // the contig is its own reverse complement
+        const unsigned long long b0 = coff[c], L = coff[c + 1] - b0;
+        if (!(comp_base(out[b0 + L - 1 - f]) < out[b0 + f])) first[c] = ~0ull;
+    }
+}
+
+// Contigs to replace: the pair of positions (a, L - 1 - a) swap, complemented.
+__global__ void __launch_bounds__(256) canon_flip_kernel(const unsigned long long* __restrict__ coff,
+                                                         const unsigned long long* __restrict__ cstart,
+                                                         unsigned long long nc, unsigned long long items,
+                                                         const unsigned long long* __restrict__ first,
+                                                         char* __restrict__ out) {
+    for (unsigned long long t = blockIdx.x * 256ull + threadIdx.x; t < items; t += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long c = item_contig(cstart, nc, t);
+        if (first[c] == ~0ull) continue;  // kept as it is
+        const unsigned long long b0 = coff[c], L = coff[c + 1] - b0, half = (L + 1) / 2;
+        const unsigned long long a0 = (t - cstart[c]) * kCanonChunk;
+        const unsigned long long a1 = a0 + kCanonChunk < half ? a0 + kCanonChunk : half;
+        for (unsigned long long a = a0; a < a1; ++a) {
+            const char x = out[b0 + a], y = out[b0 + L - 1 - a];
+            out[b0 + a] = comp_base(y);
+            out[b0 + L - 1 - a] = comp_base(x);
         }
     }
 }
 
-// contig_off[c] = first base of contig c (heads in vertex order), and the
-// total after the last (entry n of the n + 1 scanned entries).
 __global__ void __launch_bounds__(256) head_list_kernel(const unsigned long long* __restrict__ len,
                                                         const unsigned long long* __restrict__ rank,
                                                         unsigned long long n1, const unsigned long long* __restrict__ off,
@@ -284,19 +393,26 @@ static unsigned grid_for(unsigned long long n, int num_sms) {
     return g ? (unsigned)g : 1u;
 }
 
-// Scratch of a traversal of n survivors: links (2n u32), two walk buffers
-// (2n each), two ring minima and step buffers (2n each), and lengths,
-// offsets, head flags and ranks (n + 1 u64 each), scan temp.
+constexpr unsigned kMaxRounds = 33;  // jump rounds of one ranking: log2 of the ports, plus one
+
+// Scratch of a traversal of n survivors: links (2n u32), walks (2n u64), two
+// active-port lists and the ring list (2n u32 each), two ring minima (2n u32
+// each) and steps (2n u64 each), lengths, offsets, head flags and ranks
+// (n + 1 u64 each), counters, scan temp.
 size_t traverse_scratch_bytes(unsigned long long n) {
-    return 8 * n + 2 * 16 * n + 2 * (8 * n + 16 * n) + 4 * 8 * (n + 2) + scan_temp_bytes(n + 1) + 16 * 256;
+    return 8 * n + 16 * n + 3 * 8 * n + 2 * 8 * n + 2 * 16 * n + 4 * 8 * (n + 2) + 4 * 4 * (kMaxRounds + 2) +
+           scan_temp_bytes(n + 1) + 24 * 256;
 }
 
 namespace {
 struct TravBufs {
     unsigned* link;
-    Walk *wa, *wb, *sa, *sb;
+    unsigned long long* wk;
+    unsigned *act_a, *act_b, *ring;
     unsigned *ra, *rb;
+    unsigned long long *sa, *sb;
     unsigned long long *len, *off, *flag, *rank;
+    unsigned* cnt;  // jump rounds of the ranking, the ring count, jump rounds of the re-ranking
     void* temp;
 };
 
@@ -309,16 +425,19 @@ TravBufs carve_traverse(void* scratch, unsigned long long n) {
     };
     TravBufs t;
     t.link = reinterpret_cast<unsigned*>(carve(8 * n));
-    t.wa = reinterpret_cast<Walk*>(carve(16 * n));
-    t.wb = reinterpret_cast<Walk*>(carve(16 * n));
+    t.wk = reinterpret_cast<unsigned long long*>(carve(16 * n));
+    t.act_a = reinterpret_cast<unsigned*>(carve(8 * n));
+    t.act_b = reinterpret_cast<unsigned*>(carve(8 * n));
+    t.ring = reinterpret_cast<unsigned*>(carve(8 * n));
     t.ra = reinterpret_cast<unsigned*>(carve(8 * n));
     t.rb = reinterpret_cast<unsigned*>(carve(8 * n));
-    t.sa = reinterpret_cast<Walk*>(carve(16 * n));
-    t.sb = reinterpret_cast<Walk*>(carve(16 * n));
-    t.len = reinterpret_cast<unsigned long long*>(carve(8 * (n + 1)));
-    t.off = reinterpret_cast<unsigned long long*>(carve(8 * (n + 1)));
-    t.flag = reinterpret_cast<unsigned long long*>(carve(8 * (n + 1)));
-    t.rank = reinterpret_cast<unsigned long long*>(carve(8 * (n + 1)));
+    t.sa = reinterpret_cast<unsigned long long*>(carve(16 * n));
+    t.sb = reinterpret_cast<unsigned long long*>(carve(16 * n));
+    t.len = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
+    t.off = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
+    t.flag = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
+    t.rank = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
+    t.cnt = reinterpret_cast<unsigned*>(carve(4 * 4 * (kMaxRounds + 2)));
     t.temp = carve(scan_temp_bytes(n + 1));
     return t;
 }
@@ -328,17 +447,34 @@ unsigned rounds_for(unsigned long long n) {
     while ((1ull << r) <= n && r < 31) ++r;
     return r;
 }
+
+// rounds + 1 jump rounds over the list act / cnt[0], in place in wk; later
+// rounds find an empty list and return at once.
+void jump_rounds(TravBufs& t, unsigned* cnt, unsigned rounds, unsigned cap_dist, int num_sms, cudaStream_t s) {
+    unsigned *in = t.act_a, *out = t.act_b;
+    const unsigned g = (unsigned)num_sms * 16;
+    for (unsigned r = 0; r <= rounds; ++r) {
+        walk_jump_kernel<<<g, 256, 0, s>>>(t.wk, in, cnt + r, cap_dist, out, cnt + r + 1);
+        std::swap(in, out);
+    }
+}
 }  // namespace
 
 cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, const unsigned char* cls,
                                  unsigned long long n, unsigned k, const unsigned* idx, unsigned long long cap,
                                  void* scratch, unsigned long long* totals, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(totals, 0, 16, s);
+    if (n >= 0x7FFFFFFFull) return cudaErrorInvalidValue;  // port codes are 32-bit
     TravBufs t = carve_traverse(scratch, n);
     const unsigned long long ports = 2 * n;
     const unsigned g = grid_for(n, num_sms), gp = grid_for(ports, num_sms);
-    const unsigned rounds = rounds_for(n);
+    const unsigned rounds = rounds_for(ports);
     const unsigned cap_dist = 1u << rounds;  // a walk this long has gone round a ring
+    unsigned* cnt_rank = t.cnt;
+    unsigned* ring_n = t.cnt + (kMaxRounds + 2);
+    unsigned* cnt_rerank = t.cnt + 2 * (kMaxRounds + 2);
+    cudaError_t e = cudaMemsetAsync(t.cnt, 0, 4 * 4 * (kMaxRounds + 2), s);
+    if (e != cudaSuccess) return e;
     switch (W) {
         case 1: links_kernel<1><<<g, 256, 0, s>>>(keys, cls, n, k, idx, cap, t.link); break;
         case 2: links_kernel<2><<<g, 256, 0, s>>>(keys, cls, n, k, idx, cap, t.link); break;
@@ -346,32 +482,34 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
         case 4: links_kernel<4><<<g, 256, 0, s>>>(keys, cls, n, k, idx, cap, t.link); break;
         default: return cudaErrorInvalidValue;
     }
-    // list ranking; the final walks are left in t.wa
-    auto rank_walks = [&]() {
-        walk_init_kernel<<<gp, 256, 0, s>>>(t.link, ports, t.wa);
-        for (unsigned r = 0; r <= rounds; ++r) {
-            walk_double_kernel<<<gp, 256, 0, s>>>(t.wa, ports, cap_dist, t.wb);
-            std::swap(t.wa, t.wb);
-        }
-    };
-    rank_walks();
-    // rings: the smallest vertex of each, cut before it, and the ranking again
-    ring_init_kernel<<<gp, 256, 0, s>>>(t.wa, ports, cap_dist, t.link, t.ra, t.sa);
-    for (unsigned r = 0; r <= rounds; ++r) {
-        switch (W) {
-            case 1: ring_double_kernel<1><<<gp, 256, 0, s>>>(t.ra, t.sa, ports, keys, t.rb, t.sb); break;
-            case 2: ring_double_kernel<2><<<gp, 256, 0, s>>>(t.ra, t.sa, ports, keys, t.rb, t.sb); break;
-            case 3: ring_double_kernel<3><<<gp, 256, 0, s>>>(t.ra, t.sa, ports, keys, t.rb, t.sb); break;
-            case 4: ring_double_kernel<4><<<gp, 256, 0, s>>>(t.ra, t.sa, ports, keys, t.rb, t.sb); break;
-        }
-        std::swap(t.ra, t.rb);
-        std::swap(t.sa, t.sb);
-    }
-    ring_cut_kernel<<<g, 256, 0, s>>>(t.ra, n, t.link);
-    rank_walks();
-    cudaError_t e = cudaMemsetAsync(t.len + n, 0, 8, s);
+    // list ranking of every port
+    walk_init_kernel<<<gp, 256, 0, s>>>(t.link, ports, t.wk, t.act_a, cnt_rank);
+    jump_rounds(t, cnt_rank, rounds, cap_dist, num_sms, s);
+    // rings: the smallest vertex of each, cut before it, and their ports ranked again
+    ring_init_kernel<<<gp, 256, 0, s>>>(t.wk, ports, cap_dist, t.link, t.ra, t.sa, t.ring, ring_n);
+    unsigned n_ring = 0;
+    e = cudaMemcpyAsync(&n_ring, ring_n, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    chain_len_kernel<<<g, 256, 0, s>>>(t.wa, cls, n, k, t.len);
+    if (n_ring) {
+        const unsigned gr = grid_for(n_ring, num_sms), rr = rounds_for(n_ring);
+        for (unsigned r = 0; r <= rr; ++r) {
+            switch (W) {
+                case 1: ring_double_kernel<1><<<gr, 256, 0, s>>>(t.ra, t.sa, t.ring, ring_n, keys, t.rb, t.sb); break;
+                case 2: ring_double_kernel<2><<<gr, 256, 0, s>>>(t.ra, t.sa, t.ring, ring_n, keys, t.rb, t.sb); break;
+                case 3: ring_double_kernel<3><<<gr, 256, 0, s>>>(t.ra, t.sa, t.ring, ring_n, keys, t.rb, t.sb); break;
+                case 4: ring_double_kernel<4><<<gr, 256, 0, s>>>(t.ra, t.sa, t.ring, ring_n, keys, t.rb, t.sb); break;
+            }
+            std::swap(t.ra, t.rb);
+            std::swap(t.sa, t.sb);
+        }
+        ring_cut_kernel<<<gr, 256, 0, s>>>(t.ra, t.ring, ring_n, t.link);
+        walk_reinit_kernel<<<gr, 256, 0, s>>>(t.link, t.ring, ring_n, t.wk, t.act_a, cnt_rerank);
+        jump_rounds(t, cnt_rerank, rr, cap_dist, num_sms, s);
+    }
+    e = cudaMemsetAsync(t.len + n, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    chain_len_kernel<<<g, 256, 0, s>>>(t.wk, cls, n, k, t.len);
     e = exclusive_scan_u64(t.len, t.off, n + 1, t.temp, s);  // off[n] = total bases
     if (e != cudaSuccess) return e;
     head_flag_kernel<<<grid_for(n + 1, num_sms), 256, 0, s>>>(t.len, n + 1, t.flag);
@@ -380,29 +518,39 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
     e = cudaMemcpyAsync(totals, t.off + n, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(totals + 1, t.rank + n, 8, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    // the walks the writer reads: rank_walks ran an odd or even number of
-    // doublings; keep them where the writer finds them (wa of a fresh carve)
-    if (t.wa != carve_traverse(scratch, n).wa)
-        e = cudaMemcpyAsync(carve_traverse(scratch, n).wa, t.wa, 16 * n, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_traverse_write(unsigned W, const unsigned long long* keys, const unsigned char* cls,
-                                  unsigned long long n, unsigned k, void* scratch, char* out,
-                                  unsigned long long* contig_off, int num_sms, cudaStream_t s) {
+                                  unsigned long long n, unsigned k, unsigned long long n_contigs, void* scratch,
+                                  char* out, unsigned long long* contig_off, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(contig_off, 0, 8, s);
     TravBufs t = carve_traverse(scratch, n);
     const unsigned g = grid_for(n + 1, num_sms);
     head_list_kernel<<<g, 256, 0, s>>>(t.len, t.rank, n + 1, t.off, contig_off);
     switch (W) {
-        case 1: chain_write_kernel<1><<<g, 256, 0, s>>>(t.wa, cls, keys, n, k, t.off, out); break;
-        case 2: chain_write_kernel<2><<<g, 256, 0, s>>>(t.wa, cls, keys, n, k, t.off, out); break;
-        case 3: chain_write_kernel<3><<<g, 256, 0, s>>>(t.wa, cls, keys, n, k, t.off, out); break;
-        case 4: chain_write_kernel<4><<<g, 256, 0, s>>>(t.wa, cls, keys, n, k, t.off, out); break;
+        case 1: chain_write_kernel<1><<<g, 256, 0, s>>>(t.wk, cls, keys, n, k, t.off, out); break;
+        case 2: chain_write_kernel<2><<<g, 256, 0, s>>>(t.wk, cls, keys, n, k, t.off, out); break;
+        case 3: chain_write_kernel<3><<<g, 256, 0, s>>>(t.wk, cls, keys, n, k, t.off, out); break;
+        case 4: chain_write_kernel<4><<<g, 256, 0, s>>>(t.wk, cls, keys, n, k, t.off, out); break;
         default: return cudaErrorInvalidValue;
     }
-    canon_contig_kernel<<<g, 256, 0, s>>>(t.len, t.off, n, out);
+    if (n_contigs == 0) return cudaGetLastError();
+    // canonical contigs: work items of kCanonChunk first-half positions
+    // (chunk counts in flag, their starts in rank, first differences in sa)
+    const unsigned gc = grid_for(n_contigs, num_sms);
+    canon_chunks_kernel<<<gc, 256, 0, s>>>(contig_off, n_contigs, t.flag, t.sa);
+    cudaError_t e = cudaMemsetAsync(t.flag + n_contigs, 0, 8, s);
+    if (e == cudaSuccess) e = exclusive_scan_u64(t.flag, t.rank, n_contigs + 1, t.temp, s);
+    if (e != cudaSuccess) return e;
+    unsigned long long items = 0;
+    e = cudaMemcpyAsync(&items, t.rank + n_contigs, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const unsigned gi = grid_for(items, num_sms);
+    canon_diff_kernel<<<gi, 256, 0, s>>>(contig_off, t.rank, n_contigs, items, out, t.sa);
+    canon_decide_kernel<<<gc, 256, 0, s>>>(contig_off, n_contigs, out, t.sa);
+    canon_flip_kernel<<<gi, 256, 0, s>>>(contig_off, t.rank, n_contigs, items, t.sa, out);
     return cudaGetLastError();
 }
 

@@ -83,3 +83,32 @@ def test_merge_from_device_contigs(reads):
     assert_same(got, want, "merge from device contigs")
     ka.close()
     r.close()
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_merge_of_long_contigs(reads, on_device):
+    """Contigs of 60 000 and 150 000 bases (and one made of 200 reads end to
+    end): the library cuts them into overlapping pieces before extracting
+    their k-mers, which must change no k-mer, class or count of the merge."""
+    import torch
+    rng = np.random.default_rng(11)
+    pieces = [rng.choice(np.frombuffer(b"ACGT", np.uint8), L).tobytes() for L in (60_000, 150_000)]
+    pieces.append(b"".join(reads.bases[int(reads.offsets[i]):int(reads.offsets[i + 1])].tobytes()
+                           for i in range(200)))
+    pieces.append(b"ACGT")
+    contigs = np.frombuffer(b"".join(pieces), np.uint8).copy()
+    offs = np.zeros(len(pieces) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(p) for p in pieces], dtype=np.uint64)
+    for k in (31, 55):
+        r = pkg.ReadSet(reads.bases, reads.quals, reads.offsets)
+        ka = pkg.KmerAnalysis(k)
+        ka.submit(r)
+        ka.query()
+        if on_device:
+            got = ka.merge_contigs(torch.from_numpy(contigs).cuda(), torch.from_numpy(offs.view(np.int64)).cuda())
+        else:
+            got = ka.merge_contigs(contigs, offs)
+        want = oracle.merge_contigs(reads.bases, reads.quals, reads.offsets, oracle.Params(k=k), contigs, offs)
+        assert_same(got, want, f"long contigs, k={k}, device={on_device}")
+        ka.close()
+        r.close()

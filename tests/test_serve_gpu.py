@@ -191,3 +191,40 @@ def test_threads_pipelining_staged_steps():
     for th in ths:
         th.join()
     assert not errors, errors
+
+
+def test_threads_with_different_fanouts(readsets):
+    """Host threads that analyse at the same time with different partition
+    fan-outs launch the same kernels with different shared-memory sizes; the
+    kernels' shared-memory limit is one process-wide attribute, which no
+    thread may lower under another (a full-size serving run once failed a
+    scatter launch that way).  Every result equals the one taken alone."""
+    import torch
+    rs = readsets[0]
+    want = alone(rs, 31)
+    shapes = [(6, 0), (12, 3), (16, 11), (20, 9), (14, 7), (18, 11), (10, 0), (22, 11)]
+    errors = []
+
+    def worker(t):
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                for i in range(12):
+                    leaf_bits, l1_bits = shapes[(t + i) % len(shapes)]
+                    ka = pkg.KmerAnalysis(31, stream=stream, leaf_bits=leaf_bits, l1_bits=l1_bits)
+                    ka.submit(rs)
+                    got = ka.results()
+                    ka.close()
+                    try:
+                        same_result(got, want)
+                    except AssertionError:
+                        errors.append(f"thread {t}, leaf_bits {leaf_bits}, l1_bits {l1_bits}: results differ")
+        except Exception as e:  # collected: pytest sees only the main thread's failures
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors[:3]
