@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--leaf-bits", type=int, default=0)
     ap.add_argument("--gate", action="store_true", help="single: Bloom gate (k-mers seen once kept out of counting)")
     ap.add_argument("--sorted", action="store_true", help="single: survivors in ascending key order")
-    ap.add_argument("--mode", choices=["single", "batched", "serve", "multik", "large"], default="single",
+    ap.add_argument("--mode", choices=["single", "batched", "serve", "multik", "large", "assembly"], default="single",
                     help="single: the 2-Gbase metagenome (default line); batched: 64 samples of uneven size and "
                          "mixed k in one graph per wave; serve: Poisson arrivals through the serving loop")
     ap.add_argument("--scale", type=float, default=1.0, help="batched/serve: scale every sample size")
@@ -86,14 +86,15 @@ def load_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-# Source files each kernel is compiled from (its .cu and the headers it includes).
+# Source files of each kernel's device code: its .cu and the device headers it
+# includes (kernels.h holds only host-side declarations and helpers).
 KERNEL_SOURCES = {
-    "pack_kernel": ["pack.cu", "common.cuh", "kernels.h"],
-    "scatter_kernel": ["scatter.cu", "stage.cuh", "roll.cuh", "common.cuh", "kernels.h"],
-    "repart_kernel": ["repart.cu", "stage.cuh", "common.cuh", "kernels.h"],
-    "leaf_kernel": ["leaf.cu", "roll.cuh", "common.cuh", "kernels.h"],
-    "direct_insert_kernel": ["hbm.cu", "roll.cuh", "common.cuh", "kernels.h"],
-    "gate_kernel": ["gate.cu", "roll.cuh", "common.cuh", "kernels.h"],
+    "pack_kernel": ["pack.cu", "common.cuh"],
+    "scatter_kernel": ["scatter.cu", "stage.cuh", "roll.cuh", "common.cuh"],
+    "repart_kernel": ["repart.cu", "stage.cuh", "common.cuh"],
+    "leaf_kernel": ["leaf.cu", "roll.cuh", "common.cuh"],
+    "direct_insert_kernel": ["hbm.cu", "roll.cuh", "common.cuh"],
+    "gate_kernel": ["gate.cu", "roll.cuh", "common.cuh"],
 }
 
 
@@ -591,6 +592,26 @@ def assembly_record(rset, k: int, stream, s_step: int = 2, reps: int = 3) -> dic
     return out
 
 
+def run_assembly(args):
+    """The assembly sub-record alone: sort, traversal and merge on the bench
+    workload's survivors (reads resident on the device)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1809_07014_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    recipe = workload(0, args.reads)
+    rs = synth.generate(recipe)
+    dev = [torch.from_numpy(a).cuda() for a in (rs.bases, rs.quals, rs.offsets.view(np.int64))]
+    stream = torch.cuda.current_stream()
+    rset = pkg.ReadSet(*dev, stream=stream)
+    out = assembly_record(rset, args.k, stream)
+    rset.close()
+    print(json.dumps({"mode": "assembly", "config": config_of(args, recipe, rs.n_bases), **out}), flush=True)
+
+
 # --------------------------------------------------------------- batched
 BATCH_JOBS = 64
 
@@ -976,6 +997,8 @@ def main():
         run_multik(args)
     elif args.mode == "large":
         run_large(args)
+    elif args.mode == "assembly":
+        run_assembly(args)
     else:
         run_ours(args)
 

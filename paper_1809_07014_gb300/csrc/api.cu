@@ -1029,6 +1029,9 @@ int do_query(kmer_analysis* h) {
             const unsigned long long out_bytes_per = 8ull * W + 4 + 32 + 2;
             const unsigned long long bound = windows / h->p.min_count + 1024;
             unsigned long long want = h->out_hint ? h->out_hint + h->out_hint / 16 + 4096 : windows / 4 + 4096;
+            // with min_count 1 every distinct k-mer survives: size for the distinct estimate
+            if (!h->out_hint && h->p.min_count == 1)
+                want = (h->p.distinct_hint ? std::min<unsigned long long>(h->p.distinct_hint, windows) : windows) + 4096;
             if (!h->out_hint) want = std::min<unsigned long long>(want, 0.35 * (double)budget / out_bytes_per + 4096);
             if (!h->ext_out) TRY(ensure_output(h, std::min(bound, want), 0));
             // the records of a pass get what the output leaves of the budget
