@@ -14,13 +14,15 @@
 //
 //  1. links: one kernel looks up both neighbours of every vertex in the
 //     survivors' index and keeps mutual ones (port -> partner port);
-//  2. list ranking: pointer jumping over ports gives, for every port, the end
-//     reached by walking out of it and the number of steps.  The walks are
-//     updated in place (a port may read a partner's walk from this round or
-//     the last: both are true statements about the path, so the result is the
-//     same and converges at least as fast), and each round visits only the
-//     ports whose walk has not reached an end: most chains are short, so the
-//     work is far below ports x log2(n);
+//  2. list ranking, for every port the end reached by walking out of it and
+//     the number of steps, by a ruling set: about one port in 16 (by a hash)
+//     and every path start is a ruler; each ruler walks to the next ruler or
+//     the path's end, marking the ports it passes with itself and their
+//     distance from it; the rulers are then ranked by pointer jumping (in
+//     place, over the rulers not yet at an end: a port may read a partner's
+//     walk from this round or the last, both true statements about the path),
+//     and every port takes its ruler's result less its distance.  The work is
+//     about one random access per port instead of one per port and round;
 //  3. rings (ports whose walk never ends) are cut before their smallest
 //     canonical k-mer (found by doubling a running minimum around the ring),
 //     and only their ports are ranked again;
@@ -117,20 +119,8 @@ __device__ __forceinline__ void append_if(bool pred, unsigned val, unsigned* lis
     if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
-// First walks: one step to the partner's other port; linked ports go to the
-// active list.
-__global__ void __launch_bounds__(256) walk_init_kernel(const unsigned* __restrict__ link, unsigned long long ports,
-                                                        unsigned long long* __restrict__ wk, unsigned* act,
-                                                        unsigned* cnt) {
-    for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
-        const unsigned L = link[P];
-        // arriving at the partner port, the walk leaves its vertex by the other port
-        wk[P] = L == kNoPort ? walk_pack((unsigned)P, 0u) : walk_pack(L ^ 1u, 1u);
-        append_if(L != kNoPort, (unsigned)P, act, cnt);
-    }
-}
-
-// The same for the ports of a list (the rings, after their cut).
+// First walks of the ports of a list (the rings, after their cut): one step to
+// the partner's other port; linked ports go to the active list.
 __global__ void __launch_bounds__(256) walk_reinit_kernel(const unsigned* __restrict__ link,
                                                           const unsigned* __restrict__ list,
                                                           const unsigned* __restrict__ list_n,
@@ -162,6 +152,73 @@ __global__ void __launch_bounds__(256) walk_jump_kernel(unsigned long long* wk, 
             keep = d < cap_dist;
         }
         append_if(keep, P, act_out, cnt_out);
+    }
+}
+
+// Rulers: one port in 16 by a hash of its code, and every path start.
+__device__ __forceinline__ bool sampled_port(unsigned P) { return ((P * 2654435761u) >> 28) == 0u; }
+
+// Every ruler walks to the next ruler or to its path's end: owner[V] and
+// off[V] of each port V it passes (itself included) name it and V's distance
+// from it; rw[R] = (next ruler or end port, steps), and rw[E] = (E, 0) for
+// every end port E.  Rulers that have not reached an end go to the active
+// list.  Ports on rings without a ruler keep owner kNoPort.  A walk is
+// bounded by the number of ports (it cannot be longer unless the links were
+// not mutual), and one that gives up is counted in *err.
+__global__ void __launch_bounds__(256) ruler_walk_kernel(const unsigned* __restrict__ link, unsigned long long ports,
+                                                         unsigned* __restrict__ owner, unsigned* __restrict__ off,
+                                                         unsigned long long* __restrict__ rw, unsigned* act,
+                                                         unsigned* cnt, unsigned* err) {
+    for (unsigned long long P64 = blockIdx.x * 256ull + threadIdx.x; P64 < ports;
+         P64 += (unsigned long long)gridDim.x * 256) {
+        const unsigned P = (unsigned)P64;
+        const unsigned L = link[P];
+        if (L == kNoPort) rw[P] = walk_pack(P, 0u);
+        const bool ruler = link[P ^ 1u] == kNoPort || sampled_port(P);  // a path start has no predecessor
+        bool active = false;
+        if (ruler) {
+            owner[P] = P;
+            off[P] = 0;
+            if (L != kNoPort) {
+                unsigned cur = L ^ 1u, steps = 1;
+                for (;;) {
+                    if (sampled_port(cur)) break;  // the next ruler (only path starts lack a predecessor)
+                    owner[cur] = P;
+                    off[cur] = steps;
+                    const unsigned nl = link[cur];
+                    if (nl == kNoPort) break;  // the path's end
+                    if (steps >= ports) {
+                        atomicAdd(err, 1u);
+                        break;
+                    }
+                    cur = nl ^ 1u;
+                    ++steps;
+                }
+                // either a ruler (its own walk continues from there) or an end port
+                rw[P] = walk_pack(cur, steps);
+                active = true;
+            }
+        }
+        append_if(active, P, act, cnt);
+    }
+}
+
+// Every port's walk from its ruler's: the same end, less the distance from
+// the ruler; ports on rings get cap_dist.
+__global__ void __launch_bounds__(256) ruler_final_kernel(const unsigned* __restrict__ link, unsigned long long ports,
+                                                          const unsigned* __restrict__ owner,
+                                                          const unsigned* __restrict__ off,
+                                                          const unsigned long long* __restrict__ rw, unsigned cap_dist,
+                                                          unsigned long long* __restrict__ wk) {
+    for (unsigned long long P = blockIdx.x * 256ull + threadIdx.x; P < ports; P += (unsigned long long)gridDim.x * 256) {
+        const unsigned R = owner[P];
+        if (R == kNoPort) {  // a ring with no ruler
+            wk[P] = walk_pack(link[P] ^ 1u, cap_dist);
+            continue;
+        }
+        const unsigned long long w = rw[R];
+        const unsigned d = walk_dist(w);
+        wk[P] = d >= cap_dist ? walk_pack(walk_at(w), cap_dist) : walk_pack(walk_at(w), d - off[P]);
     }
 }
 
@@ -437,7 +494,7 @@ TravBufs carve_traverse(void* scratch, unsigned long long n) {
     t.off = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
     t.flag = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
     t.rank = reinterpret_cast<unsigned long long*>(carve(8 * (n + 2)));  // a scan also writes its total past the end
-    t.cnt = reinterpret_cast<unsigned*>(carve(4 * 4 * (kMaxRounds + 2)));
+    t.cnt = reinterpret_cast<unsigned*>(carve(4 * 4 * (kMaxRounds + 2)));  // three runs of counters, an error count
     t.temp = carve(scan_temp_bytes(n + 1));
     return t;
 }
@@ -450,11 +507,12 @@ unsigned rounds_for(unsigned long long n) {
 
 // rounds + 1 jump rounds over the list act / cnt[0], in place in wk; later
 // rounds find an empty list and return at once.
-void jump_rounds(TravBufs& t, unsigned* cnt, unsigned rounds, unsigned cap_dist, int num_sms, cudaStream_t s) {
+void jump_rounds(TravBufs& t, unsigned long long* walks, unsigned* cnt, unsigned rounds, unsigned cap_dist,
+                 int num_sms, cudaStream_t s) {
     unsigned *in = t.act_a, *out = t.act_b;
     const unsigned g = (unsigned)num_sms * 16;
     for (unsigned r = 0; r <= rounds; ++r) {
-        walk_jump_kernel<<<g, 256, 0, s>>>(t.wk, in, cnt + r, cap_dist, out, cnt + r + 1);
+        walk_jump_kernel<<<g, 256, 0, s>>>(walks, in, cnt + r, cap_dist, out, cnt + r + 1);
         std::swap(in, out);
     }
 }
@@ -473,6 +531,7 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
     unsigned* cnt_rank = t.cnt;
     unsigned* ring_n = t.cnt + (kMaxRounds + 2);
     unsigned* cnt_rerank = t.cnt + 2 * (kMaxRounds + 2);
+    unsigned* walk_err = t.cnt + 3 * (kMaxRounds + 2);
     cudaError_t e = cudaMemsetAsync(t.cnt, 0, 4 * 4 * (kMaxRounds + 2), s);
     if (e != cudaSuccess) return e;
     switch (W) {
@@ -482,15 +541,21 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
         case 4: links_kernel<4><<<g, 256, 0, s>>>(keys, cls, n, k, idx, cap, t.link); break;
         default: return cudaErrorInvalidValue;
     }
-    // list ranking of every port
-    walk_init_kernel<<<gp, 256, 0, s>>>(t.link, ports, t.wk, t.act_a, cnt_rank);
-    jump_rounds(t, cnt_rank, rounds, cap_dist, num_sms, s);
+    // list ranking of every port by a ruling set (owners and distances in
+    // ra / rb, the rulers' walks in sa: all free until the rings are found)
+    e = cudaMemsetAsync(t.ra, 0xFF, 4 * ports, s);
+    if (e != cudaSuccess) return e;
+    ruler_walk_kernel<<<gp, 256, 0, s>>>(t.link, ports, t.ra, t.rb, t.sa, t.act_a, cnt_rank, walk_err);
+    jump_rounds(t, t.sa, cnt_rank, rounds, cap_dist, num_sms, s);
+    ruler_final_kernel<<<gp, 256, 0, s>>>(t.link, ports, t.ra, t.rb, t.sa, cap_dist, t.wk);
     // rings: the smallest vertex of each, cut before it, and their ports ranked again
     ring_init_kernel<<<gp, 256, 0, s>>>(t.wk, ports, cap_dist, t.link, t.ra, t.sa, t.ring, ring_n);
-    unsigned n_ring = 0;
+    unsigned n_ring = 0, n_err = 0;
     e = cudaMemcpyAsync(&n_ring, ring_n, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_err, walk_err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    if (n_err) return cudaErrorUnknown;  // links that are not mutual: cannot happen
     if (n_ring) {
         const unsigned gr = grid_for(n_ring, num_sms), rr = rounds_for(n_ring);
         for (unsigned r = 0; r <= rr; ++r) {
@@ -505,7 +570,7 @@ cudaError_t launch_traverse_plan(unsigned W, const unsigned long long* keys, con
         }
         ring_cut_kernel<<<gr, 256, 0, s>>>(t.ra, t.ring, ring_n, t.link);
         walk_reinit_kernel<<<gr, 256, 0, s>>>(t.link, t.ring, ring_n, t.wk, t.act_a, cnt_rerank);
-        jump_rounds(t, cnt_rerank, rr, cap_dist, num_sms, s);
+        jump_rounds(t, t.wk, cnt_rerank, rr, cap_dist, num_sms, s);
     }
     e = cudaMemsetAsync(t.len + n, 0, 8, s);
     if (e != cudaSuccess) return e;
