@@ -260,22 +260,30 @@ const void* host_mapped(const void* p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-// A large host<->device copy in 64 MB pieces with at most two in flight
-// (the calling thread waits).  Copies in one direction share a copy engine in
+// A large host<->device copy in pieces (64 MB, at most two in flight; the
+// calling thread waits).  Copies in one direction share a copy engine in
 // submission order: a small copy that another stream submits (counters,
 // descriptors) then waits for one piece, not for the whole transfer.
+#ifndef KMER_COPY_PIECE_MB
+#define KMER_COPY_PIECE_MB 64
+#endif
+#ifndef KMER_COPY_INFLIGHT
+#define KMER_COPY_INFLIGHT 2
+#endif
 cudaError_t paced_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
-    constexpr size_t kPiece = 64ull << 20;
-    if (bytes <= 2 * kPiece) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaError_t e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+    constexpr size_t kPiece = (size_t)KMER_COPY_PIECE_MB << 20;
+    constexpr unsigned kInFlight = KMER_COPY_INFLIGHT;
+    if (bytes <= kInFlight * kPiece) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    cudaEvent_t ev[kInFlight] = {};
+    cudaError_t e = cudaSuccess;
+    for (unsigned i = 0; i < kInFlight && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     for (size_t off = 0, k = 0; e == cudaSuccess && off < bytes; off += kPiece, ++k) {
-        if (k >= 2) e = cudaEventSynchronize(ev[k & 1]);
+        if (k >= kInFlight) e = cudaEventSynchronize(ev[k % kInFlight]);
         if (e != cudaSuccess) break;
         const size_t n = bytes - off < kPiece ? bytes - off : kPiece;
         e = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, n, cudaMemcpyDefault, s);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[k & 1], s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k % kInFlight], s);
     }
     for (auto x : ev)
         if (x) cudaEventDestroy(x);
