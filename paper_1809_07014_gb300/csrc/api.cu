@@ -1463,11 +1463,13 @@ int kmer_analysis_merge_contigs(kmer_analysis_t* h, const char* contigs, const u
         // anywhere in the contigs, DEAD_END when none, FORK when several
         // A contig longer than kMergePiece bases is cut into pieces of that
         // many bases overlapping by k + 1, since one thread rolls the windows of
-        // one read and contigs can be millions of bases long.  Each window and
+        // one read and contigs can be millions of bases long (pieces of 16 k
+        // bases, at least 1024: the overlaps cost at most a sixteenth more
+        // windows, and the pieces keep the GPU's threads busy).  Each window and
         // both its extension bases then lie whole in some piece; a window at a
         // piece's edge may come twice, once without the base beyond the edge,
         // which adds no base to its sides, and counts are not used.
-        constexpr unsigned long long kMergePiece = 4096;
+        const unsigned long long kMergePiece = std::max<unsigned long long>(1024, 16ull * (h->p.k + 1));
         std::vector<unsigned long long> off(n_contigs + 1);
         if (where == KMER_DEVICE) {
             CK(cudaMemcpyAsync(off.data(), offsets, off.size() * 8, cudaMemcpyDeviceToHost, h->stream));
