@@ -204,9 +204,13 @@ struct kmer_analysis {
     // Bloom gate: filter words (log2), and first sightings / windows at hist_k
     unsigned gate_bits = 0;
     double gate_ratio = 0.0;
-    // level-1 buckets: largest fill / mean fill of the last large query at l1_imb_k
-    unsigned l1_imb_k = 0;
+    // level-1 buckets of the last large single-pass query at l1_imb_k: a high
+    // quantile of the fills over the mean, and every bucket's fill (for buckets
+    // far above the rest, such as one holding a heavy hitter)
+    unsigned l1_imb_k = 0, l1_prev_p1 = 0;
     double l1_imbalance = 0.0;
+    std::vector<unsigned long long> l1_prev_fill;
+    unsigned long long l1_prev_windows = 0;
     kmer_analysis_stats st{};
 
     unsigned W() const { return (2 * p.k + 63) / 64; }
@@ -705,7 +709,15 @@ int run_level2(kmer_analysis* h, Job j, unsigned b0, unsigned nb, unsigned long 
             std::vector<unsigned long long> fill(Pw);
             CK(cudaMemcpyAsync(fill.data(), h->l2_fill.p, Pw * 8ull, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            h->l2_slack_num = std::min(4096u, h->l2_slack_num * 3 / 2);  // future queries: more slack
+            // future queries: more slack, unless only a few leaves overflowed (heavy
+            // hitters: the exact layout below takes them; a wider slack for every
+            // leaf would only waste memory)
+            std::vector<unsigned> leafcap(nb);
+            CK(cudaMemcpyAsync(leafcap.data(), h->l2_leafcap.p, nb * 4ull, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            unsigned over = 0;
+            for (unsigned i = 0; i < Pw; ++i) over += fill[i] > leafcap[i >> g.p2];
+            if (over > std::max(4u, Pw / 64)) h->l2_slack_num = std::min(4096u, h->l2_slack_num * 3 / 2);
             exact_leaf.assign(Pw + 1, 0);
             for (unsigned i = 0; i < Pw; ++i) exact_leaf[i + 1] = exact_leaf[i] + fill[i];
             l2_capacity = exact_leaf[Pw];
@@ -757,6 +769,14 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
         // a bucket that still overflows is re-scattered with exact sizes
         const unsigned long long slack = (unsigned long long)(l1_slack(h) * (double)mean) + 1024;
         for (unsigned b = 0; b < P1; ++b) caps[b] = mean + slack;
+        // buckets that were far fuller than the rest in the last query of this
+        // shape keep their size (scaled to this query's windows)
+        if (pl.passes == 1 && h->l1_imb_k == h->p.k && h->l1_prev_p1 == g.p1 && h->l1_prev_fill.size() == P1 &&
+            h->l1_prev_windows) {
+            const double scale = (double)pass_windows / (double)h->l1_prev_windows;
+            for (unsigned b = 0; b < P1; ++b)
+                caps[b] = std::max(caps[b], (unsigned long long)(1.02 * scale * (double)h->l1_prev_fill[b]) + 1024);
+        }
     }
     const unsigned long long out_start = h->n_out;
     const double slack = (double)h->l2_slack_num / 256.0;
@@ -879,8 +899,17 @@ int run_pass(kmer_analysis* h, const Plan& pl, unsigned pass, unsigned cap_max) 
             CK(cudaStreamSynchronize(h->stream));
             const double em = (double)tot.emitted / (double)P1;
             if (em > 0) {
-                h->l1_imbalance = (double)*std::max_element(fill.begin(), fill.end()) / em;
+                // the slack of every bucket follows a high quantile (the 99th
+                // percentile), not the fullest: a heavy hitter's bucket keeps its
+                // own size from l1_prev_fill
+                std::vector<unsigned long long> sorted(fill);
+                const size_t q = P1 - 1 - P1 / 100;
+                std::nth_element(sorted.begin(), sorted.begin() + q, sorted.end());
+                h->l1_imbalance = (double)sorted[q] / em;
                 h->l1_imb_k = h->p.k;
+                h->l1_prev_p1 = g.p1;
+                h->l1_prev_fill = pl.passes == 1 ? fill : std::vector<unsigned long long>();
+                h->l1_prev_windows = tot.emitted;
             }
         }
         h->n_out = tot.out_n;

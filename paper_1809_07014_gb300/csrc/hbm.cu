@@ -35,9 +35,11 @@ size_t hbm_entry_bytes(unsigned W) {
     }
 }
 
+// Adds `mult` windows of one key with the same extension codes.
 template <int W>
 __device__ bool hbm_insert(HEntry<W>* t, unsigned long long cap, const unsigned long long (&key)[W],
-                           unsigned long long z, unsigned lcode, unsigned rcode, unsigned* status) {
+                           unsigned long long z, unsigned lcode, unsigned rcode, unsigned* status,
+                           unsigned mult = 1) {
     // home slot from the top bits of a multiplicative hash of z (the low bits
     // of a one-word z depend only on the low bits of the key)
     unsigned long long slot = (z * 0x9E3779B97F4A7C15ull) >> (__clzll(cap) + 1);
@@ -77,10 +79,10 @@ __device__ bool hbm_insert(HEntry<W>* t, unsigned long long cap, const unsigned 
             }
         }
         if (hit) {
-            const unsigned old = atomicAdd(&e->count, 1u);
-            if (old == 0xFFFFFFFFu) atomicOr(status, ST_COUNTER_OVERFLOW);
-            if (lcode) atomicAdd(&e->ext[lcode - 1], 1u);
-            if (rcode) atomicAdd(&e->ext[3 + rcode], 1u);
+            const unsigned old = atomicAdd(&e->count, mult);
+            if (old > 0xFFFFFFFFu - mult) atomicOr(status, ST_COUNTER_OVERFLOW);
+            if (lcode) atomicAdd(&e->ext[lcode - 1], mult);
+            if (rcode) atomicAdd(&e->ext[3 + rcode], mult);
             return true;
         }
         slot = (slot + 1) & (cap - 1);
@@ -114,6 +116,10 @@ __global__ void __launch_bounds__(256) direct_insert_kernel(const Job j, HEntry<
 
 // Fallback: the records of one key range of a leaf (fallback_entry), keys
 // rebuilt from the leaf's partition bits.  Counts the windows it inserts.
+// Leaves come here when they are large, which is where heavy hitters (one
+// k-mer seen millions of times, Sec. II-B) end up: the lanes of a warp holding
+// the same record (key and extension codes) add it once, with their number,
+// so a hot key costs one atomic per warp instead of one per window.
 template <int W>
 __global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const unsigned entry, HEntry<W>* t,
                                                              unsigned long long cap) {
@@ -139,16 +145,35 @@ __global__ void __launch_bounds__(256) records_insert_kernel(const Job j, const 
         recs = j.l2_rec;
     }
     unsigned windows = 0;
-    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (unsigned long long)gridDim.x * 256) {
-        unsigned long long key[W];
-        const unsigned long long tail = recs[(start + i) * W + W - 1];
-        if (rb && ((unsigned)((tail >> 6) >> shift) & rmask) != rs) continue;  // another range
+    bool stop = false;
+    for (unsigned long long i0 = blockIdx.x * 256ull; i0 < n && !stop; i0 += (unsigned long long)gridDim.x * 256) {
+        // the whole warp runs every iteration (lanes past the end or in another
+        // range hold no record), so that it can compare its records
+        const unsigned long long i = i0 + threadIdx.x;
+        unsigned long long rec[W];
+        bool have = i < n;
 #pragma unroll
-        for (int w = 0; w < W - 1; ++w) key[w] = recs[(start + i) * W + w];
-        const unsigned long long z = record_z(g, j.pass, j.bucket0 + bucket, tail);
-        key[W - 1] = z_to_tail<W>(z, key, g.bt);
-        if (!hbm_insert<W>(t, cap, key, z, ext_left(tail), ext_right(tail), j.status)) break;
-        ++windows;
+        for (int w = 0; w < W; ++w) rec[w] = have ? recs[(start + i) * W + w] : 0ull;
+        const unsigned long long tail = rec[W - 1];
+        if (have && rb && ((unsigned)((tail >> 6) >> shift) & rmask) != rs) have = false;  // another range
+        // lanes with the same record: equal in every word (a lane without one
+        // offers ~0, which no tail equals: a tail's low six bits are an
+        // extension code, at most 36)
+        unsigned peers = __match_any_sync(0xffffffffu, have ? tail : ~0ull);
+#pragma unroll
+        for (int w = 0; w < W - 1; ++w) peers &= __match_any_sync(0xffffffffu, rec[w]);
+        const unsigned lane = threadIdx.x & 31;
+        if (have && (peers & ((1u << lane) - 1u)) == 0) {  // the first lane of its group adds them all
+            unsigned long long key[W];
+#pragma unroll
+            for (int w = 0; w < W - 1; ++w) key[w] = rec[w];
+            const unsigned long long z = record_z(g, j.pass, j.bucket0 + bucket, tail);
+            key[W - 1] = z_to_tail<W>(z, key, g.bt);
+            const unsigned mult = __popc(peers);
+            if (hbm_insert<W>(t, cap, key, z, ext_left(tail), ext_right(tail), j.status, mult)) windows += mult;
+            else stop = true;
+        }
+        stop = __any_sync(0xffffffffu, stop);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) windows += __shfl_xor_sync(0xffffffffu, windows, o);
