@@ -248,6 +248,7 @@ def config_of(args, recipe, n_bases):
 # ------------------------------------------------- page-locked host buffers
 _HUGE = 512 << 20  # the largest transparent huge page here (64 KB base pages)
 _KEEP = []         # mappings registered with the driver, kept for the process
+_HUGE_FAILED = []  # registrations the driver refused
 
 
 def pinned(shape, dtype, huge: bool):
@@ -271,8 +272,14 @@ def pinned(shape, dtype, huge: bool):
     arr = np.frombuffer(m, dtype=np.uint8, count=size, offset=lead)
     arr[::65536] = 0  # fault the pages in
     rc = torch.cuda.cudart().cudaHostRegister(base + lead, size, 0)
-    if int(rc) != 0:
-        raise RuntimeError(f"cudaHostRegister failed: {rc}")
+    if int(rc) != 0:  # not registered: torch's pinned allocator instead, and say so
+        _HUGE_FAILED.append(str(rc))
+        del arr
+        try:
+            m.close()
+        except BufferError:
+            pass
+        return torch.empty(shape, dtype=getattr(torch, np.dtype(dtype).name)).pin_memory()
     _KEEP.append(m)
     return torch.from_numpy(arr[:n].view(dtype).reshape(shape))
 
@@ -528,7 +535,9 @@ def run_ours(args):
                        "host_io": ("KMER_HOST_STAGED (copy engines), one step counting at a time" if staged
                                    else "KMER_HOST (in place)"),
                        "host_buffers": ("anonymous memory advised for 512 MB transparent huge pages, registered "
-                                        "with the driver" if args.e2e_alloc == "huge" else "torch pinned allocator"),
+                                        "with the driver" if args.e2e_alloc == "huge" and not _HUGE_FAILED
+                                        else "torch pinned allocator" + (f" (registration refused: {_HUGE_FAILED[0]})"
+                                                                         if _HUGE_FAILED else "")),
                        "one_thread": {"value": w1 / dt1, "ms_per_step": 1e3 * dt1 / args.steps,
                                       "host_io": "KMER_HOST (in place)"}}
         for ln in lanes:
