@@ -138,7 +138,7 @@ typedef struct {
  * same as the lexicographic order of the k-mers) with count, ext and cls
  * moved along: a least-significant-digit radix sort on the device, 2k/8
  * passes over the keys, in place in the result arrays.  Its scratch (about
- * 8W + 52 bytes per survivor) reuses the query's record buffers when they are
+ * 8W + 74 bytes per survivor) reuses the query's record buffers when they are
  * large enough.  query_into with page-locked host arrays (KMER_HOST) then
  * stages through the analysis's device buffers as with KMER_HOST_STAGED.
  * At most 2^32 - 2 survivors (INVALID_ARG beyond).  Ignored by batches. */
