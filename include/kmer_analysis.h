@@ -246,8 +246,9 @@ int kmer_analysis_submit_raw(kmer_analysis_t *h, const char *bases, const uint8_
  * (steps a2-a7) and fills *out with device pointers to the survivors, in no
  * particular order (ascending key order with KMER_FLAG_SORTED_OUTPUT).
  * Synchronises the stream.  Buffers grow as needed and are kept for the next
- * query.  Errors: OOM, TABLE_FULL, COUNTER_OVERFLOW,
- * TIMEOUT, CUDA; the previous results are invalid after an error. */
+ * query.  Errors: OOM, TABLE_FULL, COUNTER_OVERFLOW, TIMEOUT, CUDA, and
+ * INVALID_ARG for sorted output of more than 2^32 - 2 survivors; the
+ * previous results are invalid after an error. */
 int kmer_analysis_query(kmer_analysis_t *h, kmer_result_view *out);
 
 /* As kmer_analysis_query, but the survivors are written straight into the
