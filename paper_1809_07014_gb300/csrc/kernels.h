@@ -13,7 +13,9 @@ namespace kmer {
 // A kernel's dynamic shared-memory limit is one attribute per function and
 // device, shared by every host thread: raise it to `bytes` when it is lower,
 // never lower it (a thread that lowered it could make another thread's launch
-// with a larger size fail).
+// with a larger size fail).  The limits set are remembered per process; a
+// cudaDeviceReset() by the application clears the attributes but not this
+// record, so such an application must not reset a device it still analyses on.
 inline cudaError_t raise_smem_limit(const void* func, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<int, const void*>, size_t> limit;
